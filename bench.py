@@ -1,0 +1,418 @@
+"""Benchmark: particle-timeslices/s of the path action + adjoint gradient.
+
+One step = one whole-path Metropolis-adjusted Langevin update of every chain
+(proposal from the path gradient -> action and adjoint gradient of the proposal
+-> FP64 Metropolis-Hastings test -> accept/commit), i.e. every stage of the hot
+path.  A step evaluates the action and gradient once per chain, so it processes
+N * T particle-timeslices per chain.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config lj500|ho3d|lj108|ragged|ho1d]
+                  [--impl ours|reference]
+
+--impl reference times the CPU oracle (the slow plain FP64 program the GPU path
+is checked against) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle-timeslices/s for path action+adjoint gradient, batched vs plain GPU"
+UNIT = "particle-timeslices/s"
+# Algorithmic flop count of the LJ action + adjoint (FMA = 2, rsqrt/rint = 1):
+# per unordered in-cutoff pair 44 for the force and 31 for the Hessian-vector
+# product; per particle-timeslice 23 for residual, |r|^2 and gradient assembly.
+FLOPS_PER_PAIR = 75
+FLOPS_PER_UNIT = 23
+# Harmonic action + gradient: read x once, write g once per coordinate.
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="lj500")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--h", type=float, default=0.0, help="MALA step (0: per-config default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+DEFAULT_H = {"lj500": 2e-7, "lj108": 5e-7, "ragged": 2e-7, "ho3d": 1e-5, "ho1d": 1e-4}
+
+
+def workload_desc(w):
+    import pamd_inputs as inputs  # noqa: F401
+    s = w.systems
+    if w.name == "ragged":
+        return (f"ragged: {len(s)} LJ systems, N in [{min(x.N for x in s)},{max(x.N for x in s)}], "
+                f"T in [{min(x.T for x in s)},{max(x.T for x in s)}], rho=0.85, T*=1, rc=min(2.5,L/2), "
+                f"D=1, dt={w.dt}, EM start paths")
+    x = s[0]
+    if x.kind == "lj":
+        return (f"{w.name}: LJ liquid N={x.N}, rho=0.85, T*=1, rc={x.rc_eff:g}, box={x.box:.4f}, "
+                f"T={x.T} steps, {x.n_chains} chains, D=1, dt={w.dt}, FCC + Euler-Maruyama start path")
+    return (f"{w.name}: {x.d}D harmonic oscillator k=1, T={x.T} steps, {x.n_chains} chains, "
+            f"D=1, beta=1, dt={w.dt}, start path {w.init}")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lj_kernels.cu", "ho_kernels.cu", "pamd_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1907_09529_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(config, kernel):
+    """DRAM bytes per launch recorded from an ncu capture of the current kernel source
+    (profiles/traffic.json), or None if the kernels changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(config, {})
+    if ent.get("kernel") != kernel or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(w, budget_s=12.0):
+    """Time the CPU oracle's action+gradient on a bounded sample of the workload:
+    one chain of the (first) system, slices grown until ~budget_s of CPU work."""
+    import oracle
+    import pamd_inputs as inputs
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    spec = w.systems[0]
+    if w.name == "ragged":
+        spec = max(w.systems, key=lambda s: s.N)
+    pot = (oracle.lennard_jones(spec.box, spec.rc_eff) if spec.kind == "lj"
+           else oracle.harmonic(spec.k))
+    nth = oracle.max_threads()
+
+    def run(T):
+        T = min(T, spec.T)
+        s1 = inputs.SystemSpec(spec.kind, spec.N, spec.d, T, 1)
+        if spec.kind == "lj":
+            x0 = inputs.initial_positions(s1, 1)
+            xi = inputs.euler_noise(s1, 2)
+            path = oracle.euler_batch(pot, x0, xi, w.D, w.beta, w.dt, store_f32=True)[0]
+        else:
+            path = inputs.gaussian_path(3, 1, T, spec.d, spec.N, 1.0)[0]
+        t0 = time.perf_counter()
+        oracle.action_grad(pot, path, w.D, w.beta, w.dt, nthreads=nth)
+        return T, time.perf_counter() - t0
+
+    T, dtm = run(8 if spec.kind == "lj" else 4096)
+    while dtm < budget_s / 8 and T < spec.T:
+        T, dtm = run(min(spec.T, int(T * max(2.0, budget_s / max(dtm, 1e-3) / 4))))
+    if dtm < budget_s / 3 and T < spec.T:
+        T, dtm = run(min(spec.T, int(T * budget_s / max(dtm, 1e-3))))
+    units = spec.N * T
+    return {"value": units / dtm, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": f"1 chain of {spec.kind} N={spec.N}, {T} of {spec.T} steps, action+gradient "
+                      f"({dtm:.1f} s, OpenMP over slices)"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times, res = [], None
+    for i in range(args.warmup + args.steps):
+        res = oracle_sample(w, budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if i >= args.warmup:
+            times.append(1.0 / res["value"])
+    v = 1.0 / statistics.mean(times)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_desc(w)},
+           "cpu_baseline": {**res, "value": v},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def launches_per_update(prob):
+    n_lj = sum(1 for s in prob.systems if s.kind == "lj")
+    n_ho = 1 if any(s.kind == "harmonic" for s in prob.systems) else 0
+    # propose, [harmonic action], LJ action per system, finalize S, reverse,
+    # finalize q_fwd, finalize q_rev, accept, commit
+    return 1 + n_ho + n_lj + 1 + 1 + 2 + 1 + 1
+
+
+def main():
+    args = parse()
+    import pamd_inputs as inputs
+    w = inputs.workload(args.config)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    import paper_1907_09529_gb300 as pamd
+
+    systems = []
+    for s in w.systems:
+        if s.kind == "lj":
+            systems.append(pamd.System("lj", s.N, s.d, s.T, s.n_chains, box=s.box, rc=s.rc_eff))
+        else:
+            systems.append(pamd.System("harmonic", s.N, s.d, s.T, s.n_chains, k=s.k))
+    prob = pamd.Problem(systems, w.D, w.beta, w.dt, "fp32")
+    stream = torch.cuda.current_stream(dev)
+
+    # Start paths, built on the device: Gaussian slices or Euler-Maruyama from FCC / 0.
+    seed = w.seed * 100 + rank
+    pos = prob.empty(dev)
+    for q, s in enumerate(w.systems):
+        v = prob.view(pos, q)
+        if w.init == "gaussian":
+            g = torch.Generator(device=dev)
+            g.manual_seed(seed + q)
+            v.copy_(torch.randn(v.shape, generator=g, device=dev) / math.sqrt(w.beta * s.k))
+        else:
+            v[:, 0].copy_(torch.from_numpy(inputs.initial_positions(s, seed)).to(dev))
+    if w.init != "gaussian":
+        pamd.euler_reference(prob, pos, seed=seed, counter=0)
+    S, grad = pamd.action_grad(prob, pos)
+    torch.cuda.synchronize()
+    h = args.h if args.h > 0 else DEFAULT_H.get(w.name, 1e-6)
+    nacc = torch.zeros(prob.n_chains, dtype=torch.int32, device=dev)
+    units_rank = prob.units
+
+    def step(i):
+        pamd.path_update(prob, pos, grad, S, h, 1, seed=seed, counter=1000 + i, n_accepted=nacc)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = units_rank * world * args.steps / (ms_max * 1e-3)
+
+    # Dominant kernel: the action + adjoint kernel alone (one launch per LJ system
+    # + a tiny finalize), timed with events on its stream over the same data.
+    nk = 10
+    gk = torch.empty_like(pos)
+    Sk = torch.empty_like(S)
+    pamd.action_grad(prob, pos, Sk, gk)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nk):
+        pamd.action_grad(prob, pos, Sk, gk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_kernel = e0.elapsed_time(e1) / nk
+
+    has_lj = any(s.kind == "lj" for s in w.systems)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    if has_lj:
+        counts = pamd.lj_pair_counts(prob, pos)
+        pairs = 0
+        off = 0
+        for s in w.systems:
+            nsl = s.n_chains * (s.T + 1)
+            c = counts[off:off + nsl].view(s.n_chains, s.T + 1)[:, :s.T]
+            pairs += int(c.sum().item()) // 2
+            off += nsl
+        flops = FLOPS_PER_PAIR * pairs + FLOPS_PER_UNIT * units_rank
+        achieved = flops / (ms_kernel * 1e-3) / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(args.config, "lj_action_kernel"),
+                "kernel": "lj_action_kernel<float,TPP,true>",
+                "peak_note": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
+                "pairs_per_launch": pairs, "flops_per_launch": flops, "kernel_ms": ms_kernel}
+    else:
+        nbytes = sum(s.n_chains * (s.T + 1) * s.d * s.N for s in w.systems) * 4 * 2
+        achieved = nbytes / (ms_kernel * 1e-3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": profiled_traffic(args.config, "ho_action_kernel"),
+                "kernel": "ho_action_kernel<float,true>", "peak_note":
+                "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
+                "bytes_per_launch": nbytes, "kernel_ms": ms_kernel}
+
+    # Plain single-path FP64 form of the same action + gradient (one chain per launch).
+    plain = None
+    if not args.no_plain and rank == 0:
+        p64 = pamd.Problem(systems, w.D, w.beta, w.dt, "fp64", one_chain_per_launch=True)
+        pos64 = pos.double()
+        S64, g64 = pamd.action_grad(p64, pos64)
+        torch.cuda.synchronize()
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            pamd.action_grad(p64, pos64, S64, g64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / reps
+        relS = float(((S64 - Sk).abs() / S64.abs()).max().item())
+        relG = float(((g64.float() - gk).norm() / g64.norm()).item())
+        plain = {"value": units_rank / (ms64 * 1e-3), "unit": UNIT, "ms_per_call": ms64,
+                 "batched_fp32_ms_per_call": ms_kernel,
+                 "speedup_batched_vs_plain": ms64 / ms_kernel,
+                 "fp32_vs_fp64_rel_err_S": relS, "fp32_vs_fp64_rel_err_grad": relG}
+        del pos64, S64, g64
+
+    # End to end through the C ABI with host buffers: every step copies the path,
+    # its cached gradient and action to the device and the updated ones back.
+    e2e = None
+    if not args.no_e2e:
+        hpos = pos.cpu().pin_memory()
+        hgrad = grad.cpu().pin_memory()
+        hS = S.cpu().pin_memory()
+        hacc = torch.zeros(prob.n_chains, dtype=torch.int32).pin_memory()
+        pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=5, n_accepted=hacc)
+        ne = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(ne):
+            pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=6 + i, n_accepted=hacc)
+        t_e2e = (time.perf_counter() - t0) / ne
+        nbuf = prob.span * 4
+        e2e = {"value": units_rank * world / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
+               "d2h_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
+               "ms_per_step": t_e2e * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(w), "precision": "FP32 data, FP64 accumulation",
+                       "units_per_step_per_gpu": units_rank, "mala_h": h,
+                       "l2": "inputs larger than L2 (no flush needed)"
+                       if prob.span * 4 * 4 > 129e6 else "inputs smaller than L2",
+                       "parallelism": f"chains sharded over {world} GPU(s), no collective"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plain_fp64": plain,
+            "gpu_launches": args.steps * (launches_per_update(prob)) + 1 * args.steps,
+            "clocks": clk, "accept_rate": float(nacc.sum().item()) / max(
+                1, prob.n_chains * (args.steps + args.warmup)),
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * pamd.h -- C ABI of libpamd, the GB300 (sm_103a) path-action library for
+ * path-accelerated molecular dynamics (Rosa-Raices, Zhang & Miller,
+ * arXiv:1907.09529).
+ *
+ * The library evaluates, for every timeslice of whole Brownian-dynamics
+ * paths at once, the force F(x_t), the Euler-Maruyama residual
+ *     r_t = x_{t+1} - x_t - beta D dt F(x_t)                   (Sec. II.A, Eq. (3))
+ * the action
+ *     S = sum_{t=0}^{T-1} |r_t|^2 / (4 D dt)                    (Eq. (4), unnormalised)
+ * and its path gradient
+ *     dS/dx_t = [r_{t-1} - r_t + beta D dt H(x_t) r_t] / (2 D dt),  r_{-1} = r_T = 0,
+ * with H the Hessian of the potential (Eq. (1): drift -gamma^-1 V',
+ * D = 1/(beta gamma)).  The normalisation of the short-time propagator of
+ * Eq. (3) is dropped; it does not depend on the path.
+ *
+ * Data layout.  A chain's path is T+1 slices, each slice [dim][N] (all
+ * x coordinates of the particles, then all y, then all z):
+ *     pos[t][c][n],  element index (t*dim + c)*N + n.
+ * A system's chains follow one another contiguously starting at element
+ * `pos_offset` of the buffer; gradients use exactly the same layout.
+ * Chains are numbered globally in system order; per-chain arrays (S,
+ * acceptance counters, ...) are indexed by that number.
+ *
+ * Precision.  PAMD_FP32: positions, forces, residuals and gradients are
+ * float; every action, acceptance term and Metropolis comparison is
+ * accumulated and taken in double.  PAMD_FP64: everything is double
+ * ("plain" form).  The position/gradient buffers hold the element type of
+ * the chosen precision.
+ *
+ * Pointers.  Unless stated otherwise a pointer argument may be a device
+ * pointer or a host pointer.  Device pointers must be allocated by the
+ * caller (the library never frees them).  If ANY buffer argument of a call
+ * is a host pointer, the library copies inputs to its own device workspace,
+ * runs, copies results back, and synchronises `stream` before returning.
+ * With device pointers every call is asynchronous on `stream`.  Device
+ * buffers must be 16-byte aligned.
+ *
+ * Errors.  Every entry point returns PAMD_OK (0) or a negative status; no
+ * C++ exception crosses this boundary.  On error nothing is guaranteed
+ * about the output buffers.
+ *
+ * First use.  The first call for a given problem shape builds a plan and
+ * allocates its device workspace (cudaMalloc); make that first call before
+ * any stream capture.  pamd_release_cache() frees all of it.
+ */
+#ifndef PAMD_H
+#define PAMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PAMD_OK 0
+#define PAMD_ERR_ARG (-1)          /* invalid argument or shape */
+#define PAMD_ERR_UNSUPPORTED (-2)  /* valid, but outside what the kernels handle */
+#define PAMD_ERR_CUDA (-3)         /* a CUDA runtime call or launch failed */
+#define PAMD_ERR_TIMEOUT (-4)      /* a bounded device wait ran out */
+#define PAMD_ERR_NONFINITE (-5)    /* a non-finite action was produced */
+#define PAMD_ERR_ALLOC (-6)        /* workspace allocation failed */
+
+/* Potential kinds. */
+#define PAMD_HARMONIC 0  /* V = k/2 |x|^2 per coordinate (Sec. IV.A, isotropic in dim) */
+#define PAMD_LJ 1        /* cut-and-force-shifted Lennard-Jones, Eq. (11), periodic cube */
+
+/* Precisions. */
+#define PAMD_FP32 0      /* float data, double accumulation of S and acceptance terms */
+#define PAMD_FP64 1      /* double everywhere */
+
+/* Potential parameters (Eq. (11): U(r) = u(r) - u(rc) - (r - rc) u'(rc) for r <= rc,
+ * u(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6]).  For PAMD_LJ, 0 < rc <= box/2 is
+ * required (only the nearest periodic image can then interact) and dim must be 3.
+ * For PAMD_HARMONIC only k is read. */
+typedef struct {
+    int kind;
+    double k;
+    double eps, sigma, rc, box;
+} pamd_potential;
+
+/* One system: n_chains independent paths of n_steps steps (n_steps+1 slices)
+ * of n_particles particles in dim dimensions.  Supported: 1 <= dim <= 3,
+ * n_steps >= 1; PAMD_LJ: 2 <= n_particles <= 1024. */
+typedef struct {
+    int n_particles;
+    int n_steps;
+    int dim;
+    int n_chains;
+    long long pos_offset;  /* element offset of chain 0, slice 0 in pos/grad buffers */
+    pamd_potential pot;
+} pamd_system;
+
+/* A batch of systems sharing D, beta, dt (paper notation; dt is the path
+ * discretisation step, beta the inverse temperature, D the diffusion
+ * coefficient).  `systems` is a host array of n_systems entries. */
+typedef struct {
+    double D, beta, dt;
+    int n_systems;
+    const pamd_system* systems;
+    int precision;  /* PAMD_FP32 or PAMD_FP64 */
+    int flags;      /* 0, or PAMD_FLAG_* below */
+} pamd_problem;
+
+/* Run one chain per launch (the "plain" single-path form). */
+#define PAMD_FLAG_ONE_CHAIN_PER_LAUNCH 1
+
+/* Action S of every chain (Eqs. (3)-(4)).
+ *   pos : path buffer (precision's element type), layout above.
+ *   S   : double[n_chains_total], written.
+ * Returns PAMD_OK or an error status. */
+int pamd_action(const pamd_problem* prob, const void* pos, double* S, void* stream);
+
+/* Action and path gradient of every chain (Eqs. (3)-(4) differentiated).
+ *   pos  : path buffer, read.
+ *   S    : double[n_chains_total], written.
+ *   grad : same layout and type as pos, written for all T+1 slices (x_0
+ *          included; masking the fixed tail is the caller's business). */
+int pamd_action_grad(const pamd_problem* prob, const void* pos, double* S, void* grad,
+                     void* stream);
+
+/* n_updates successive whole-path Metropolis-adjusted Langevin updates of
+ * every chain, consuming the path gradient; the tail slice x_0 is held
+ * fixed and the update is accepted by the Metropolis-Hastings test (the
+ * paper's path-sampling move, Sec. III, with a gradient-informed trial):
+ *     x'_t = x_t - h g_t + sqrt(2h) eta_t  (t >= 1),   x'_0 = x_0,
+ *     log alpha = S(x) - S(x') - |x - x' + h g(x')|^2/(4h) + |x' - x + h g(x)|^2/(4h)
+ * (sums over t >= 1), accepted iff log u < log alpha, all in double.
+ *   pos, grad, S : in/out.  On entry grad and S must hold the gradient and
+ *                  action of pos (from pamd_action_grad); on return they
+ *                  hold those of the updated path.
+ *   h            : step size (> 0).
+ *   seed,counter : Philox4x32-10 key and counter; update u uses counter+u.
+ *   noise        : NULL (normals drawn from Philox, stream 1) or, only with
+ *                  n_updates == 1, standard normals eta in the layout of pos
+ *                  (slice-0 entries ignored), element type of the precision.
+ *   log_u        : NULL (uniforms from Philox, stream 2) or, only with
+ *                  n_updates == 1, double[n_chains_total] of log uniforms.
+ *   n_accepted   : int[n_chains_total], incremented by accepted updates (may be NULL).
+ *   log_alpha    : double[n_chains_total], log alpha of the last update (may be NULL).
+ * With device pointers and n_updates > 1 the updates are captured once into
+ * a CUDA graph (cached per shape) and replayed. */
+int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S, double h,
+                     int n_updates, uint64_t seed, uint64_t counter, const void* noise,
+                     const double* log_u, int* n_accepted, double* log_alpha, void* stream);
+
+/* Forward Euler-Maruyama paths (Eq. (2)), sequential in time:
+ *     x_{t+1} = x_t + beta D dt F(x_t) + sqrt(2 D dt) xi_t,
+ * each new slice stored in the precision's element type and used as stored.
+ *   pos   : in/out; slice 0 of every chain holds x_0 on entry, slices 1..T
+ *           are written.
+ *   noise : NULL (normals from Philox, stream 0, seed/counter) or standard
+ *           normals in the layout of pos, slice t+1 holding xi_t (slice-0
+ *           entries ignored). */
+int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uint64_t counter,
+                         const void* noise, void* stream);
+
+/* Diagnostics for bit-exact index parity: number of ordered in-cutoff pairs
+ * (i != j) of every slice of every LJ chain, decided in single precision by
+ * the kernels' rule (dx = xi - xj; dx = fmaf(-L, rintf(dx * (1/L)), dx);
+ * r2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx)); in iff r2 <= rc*rc), with
+ * L, 1/L, rc*rc rounded to float.  PAMD_FP32 problems only.
+ *   counts : long long[sum over LJ chains of (T+1)], chain-major, written. */
+int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* counts,
+                        void* stream);
+
+/* Raw Philox4x32-10 output (Salmon et al., SC'11) for n consecutive
+ * counters: block q uses counter (ctr0 + q, ctr1, ctr2, ctr3), key (key0, key1);
+ * out: uint32[4 n], written (device or host). */
+int pamd_philox(uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3, uint32_t key0,
+                uint32_t key1, long long n, uint32_t* out, void* stream);
+
+/* Standard normals of the library's noise streams for elements e0..e0+n-1
+ * of one chain (the same values pamd_path_update / pamd_euler_reference
+ * draw): Philox4x32-10 with counter (e/4, chain, counter_lo,
+ * counter_hi16 | stream<<16) and key (seed_lo, seed_hi); the four words
+ * give 24-bit uniforms u = ((w>>8)+1)/2^24 (words 0, 2) and v = (w>>8)/2^24
+ * (words 1, 3); z = sqrt(-2 ln u) (cos, sin)(2 pi v) in single precision.
+ *   out : float[n], written. */
+int pamd_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain,
+                 long long e0, long long n, float* out, void* stream);
+
+/* Launch-shape override for the Lennard-Jones kernels (0 or a negative skin
+ * keeps the automatic choice): steps per CTA tile, threads per particle
+ * (1, 2 or 4), neighbour-list capacity per particle, Verlet skin (sigma
+ * units).  Affects plans built afterwards; results do not depend on these
+ * (candidate order is fixed), only speed.  Host-side setting, not thread-safe
+ * against concurrent calls. */
+int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin);
+
+/* Human-readable name of a status code (static string). */
+const char* pamd_status_string(int status);
+
+/* Free every cached plan, workspace and graph (synchronises the device). */
+int pamd_release_cache(void);
+
+/* Library version, for the bindings. */
+int pamd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAMD_H */

@@ -446,11 +446,14 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 }
 
 /* Standard normals for element e of one chain's noise stream.
- * Counter = (e/2, chain, counter_lo, counter_hi16 | stream<<16),
- * key = (seed_lo, seed_hi).  The four words give two 53-bit uniforms
- * u1 in (0,1], u2 in [0,1); Box-Muller in double precision:
- * z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2);
- * element e takes z_(e mod 2). */
+ * Counter = (e/4, chain, counter_lo, counter_hi16 | stream<<16),
+ * key = (seed_lo, seed_hi).  Each of the four words gives a 24-bit
+ * uniform: u = ((w >> 8) + 1) 2^-24 in (0,1] for words 0 and 2,
+ * v = (w >> 8) 2^-24 in [0,1) for words 1 and 3.  Box-Muller, evaluated
+ * here in double precision:
+ *   z0 = sqrt(-2 ln u0) cos(2 pi v1), z1 = sqrt(-2 ln u0) sin(2 pi v1),
+ *   z2 = sqrt(-2 ln u2) cos(2 pi v3), z3 = sqrt(-2 ln u2) sin(2 pi v3);
+ * element e takes z_(e mod 4). */
 void or_normals(uint64_t seed, uint64_t counter, uint32_t stream, uint32_t chain,
                 int64_t e0, int64_t n, double* out)
 {
@@ -458,14 +461,17 @@ void or_normals(uint64_t seed, uint64_t counter, uint32_t stream, uint32_t chain
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int64_t q = 0; q < n; ++q) {
         int64_t e = e0 + q;
-        uint32_t ctr[4] = {(uint32_t)(e >> 1), chain, (uint32_t)counter,
+        uint32_t ctr[4] = {(uint32_t)(e >> 2), chain, (uint32_t)counter,
                            (uint32_t)((counter >> 32) & 0xFFFFu) | (stream << 16)};
         uint32_t w[4];
         or_philox4x32_10(ctr, key, w);
-        double u1 = ((double)((uint64_t)(w[0] >> 5) * 67108864u + (w[1] >> 6)) + 1.0) * 0x1p-53;
-        double u2 = (double)((uint64_t)(w[2] >> 5) * 67108864u + (w[3] >> 6)) * 0x1p-53;
-        double rad = sqrt(-2.0 * log(u1));
-        out[q] = (e & 1) ? rad * sin(two_pi * u2) : rad * cos(two_pi * u2);
+        int lane = (int)(e & 3);
+        uint32_t wu = (lane < 2) ? w[0] : w[2];
+        uint32_t wv = (lane < 2) ? w[1] : w[3];
+        double u = ((double)(wu >> 8) + 1.0) * 0x1p-24;
+        double v = (double)(wv >> 8) * 0x1p-24;
+        double rad = sqrt(-2.0 * log(u));
+        out[q] = (lane & 1) ? rad * sin(two_pi * v) : rad * cos(two_pi * v);
     }
 }
 

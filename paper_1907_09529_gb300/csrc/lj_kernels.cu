@@ -1,0 +1,540 @@
+// lj_kernels.cu -- Lennard-Jones path action and adjoint gradient, Euler-Maruyama
+// reference paths, and the single-precision pair-count diagnostic.
+//
+// Pair potential (paper Eq. (11)), cut and force shifted:
+//   U(r) = u(r) - u(rc) - (r - rc) u'(rc)  (r <= rc),  u = 4 eps[(s/r)^12 - (s/r)^6].
+// With S6 = (sigma/r)^6 and ir2 = 1/r^2:
+//   u'(r)/r = 24 eps ir2 S6 (1 - 2 S6),   u''(r) = 24 eps ir2 S6 (26 S6 - 7),
+//   U'(r)/r = u'(r)/r - u'(rc)/r,          U''(r) = u''(r).
+// Force on i:  F_i = -sum_j (U'(r)/r) r_ij,  r_ij = x_i - x_j (minimum image).
+// Hessian-vector product:  (Hv)_i = sum_j [ (U'/r) v_ij + ((U'' - U'/r)/r^2)(r_ij . v_ij) r_ij ],
+// v_ij = v_i - v_j.  With a = beta D dt:
+//   r_t = x_{t+1} - x_t - a F(x_t)                          (Eq. (3))
+//   g_t = [r_{t-1} - r_t + a H(x_t) r_t] / (2 D dt),  r_{-1} = r_T = 0.
+//
+// Work decomposition.  One CTA per (chain, tile of TS consecutive steps).  The
+// current slice x_t and the next x_{t+1} live in shared memory as 4-vectors, as
+// does r_t (the Hessian-vector product needs the residuals of the neighbours).
+// Each particle owns TPP adjacent threads; thread q of particle i handles the
+// candidates j = q (mod TPP).  A Verlet list of radius rc + skin, built from the
+// slice at the tile start, is kept in shared memory and reused for the following
+// slices: it stays exact while no particle has moved more than skin/2 from the
+// position it had when the list was built (then no pair can have crossed from
+// outside rc + skin to inside rc); otherwise the CTA rebuilds it.  A particle
+// whose list overflows the capacity scans all candidates instead.  Candidates are
+// visited in increasing j in either case, so every sum has the same order no
+// matter when the list was (re)built: results do not depend on the tiling.
+// The residual of the step before the tile (r_{t0-1}) is recomputed locally.
+#include "pamd_internal.cuh"
+
+namespace pamd {
+
+template <typename R>
+struct LJK {
+    R L, iL, rc2, rl2, hs2;  // box, 1/box, rc^2, list radius^2, (skin/2)^2
+    R e24, sig6, duc;        // 24 eps, sigma^6, u'(rc)
+    R a, ginv, sig_em;       // beta D dt, 1/(2 D dt), sqrt(2 D dt)
+};
+
+template <typename R>
+static LJK<R> make_lj_consts(const LJConst& c, double sig_em)
+{
+    LJK<R> k;
+    const double rl = c.rc + c.skin;
+    const double s6 = c.sigma * c.sigma * c.sigma * c.sigma * c.sigma * c.sigma;
+    const double src = c.sigma / c.rc;
+    const double q6 = src * src * src * src * src * src;
+    // u'(rc) = 4 eps (-12 (s/rc)^12 + 6 (s/rc)^6) / rc
+    const double duc = 4.0 * c.eps * (-12.0 * q6 * q6 + 6.0 * q6) / c.rc;
+    if (sizeof(R) == sizeof(float)) {
+        // The single-precision cutoff rule: L, 1/L and rc^2 rounded to float.
+        const float Lf = (float)c.L;
+        const float rcf = (float)c.rc;
+        k.L = (R)Lf;
+        k.iL = (R)(1.0f / Lf);
+        k.rc2 = (R)(rcf * rcf);
+    } else {
+        k.L = (R)c.L;
+        k.iL = (R)(1.0 / c.L);
+        k.rc2 = (R)(c.rc * c.rc);
+    }
+    k.rl2 = (R)(rl * rl);
+    k.hs2 = (R)(0.25 * c.skin * c.skin);
+    k.e24 = (R)(24.0 * c.eps);
+    k.sig6 = (R)s6;
+    k.duc = (R)duc;
+    k.a = (R)c.a;
+    k.ginv = (R)c.ginv;
+    k.sig_em = (R)sig_em;
+    return k;
+}
+
+// Minimum-image pair vector and |r_ij|^2 by the documented rule.
+template <typename R>
+__device__ __forceinline__ R pair_r2(R xi, R yi, R zi, const vec4_t<R>& pj, const LJK<R>& k, R& dx,
+                                     R& dy, R& dz)
+{
+    dx = xi - pj.x;
+    dy = yi - pj.y;
+    dz = zi - pj.z;
+    dx = fma_r(-k.L, rint_r(mul_r(dx, k.iL)), dx);
+    dy = fma_r(-k.L, rint_r(mul_r(dy, k.iL)), dy);
+    dz = fma_r(-k.L, rint_r(mul_r(dz, k.iL)), dz);
+    return fma_r(dz, dz, fma_r(dy, dy, mul_r(dx, dx)));
+}
+
+// -U'(r)/r for r^2 <= rc^2 (ri = 1/r, ir2 = 1/r^2).
+template <typename R>
+__device__ __forceinline__ R force_scalar(R ri, R ir2, const LJK<R>& k, R& s6_out)
+{
+    const R s6 = k.sig6 * ir2 * ir2 * ir2;
+    s6_out = s6;
+    return fma_r(k.e24 * ir2 * s6, R(2) * s6 - R(1), k.duc * ri);
+}
+
+template <typename R, int TPP>
+struct LJBlock {
+    using V4 = vec4_t<R>;
+    int N, NT, tid, i, q, cap;
+    bool active;
+    uint16_t* nbr;  // nbr[m * NT + tid], m < cap
+    int cnt;
+    bool ovf;
+    R xr, yr, zr;   // position at the last list build
+
+    __device__ void build(const V4* __restrict__ buf, const LJK<R>& k)
+    {
+        cnt = 0;
+        ovf = false;
+        if (!active) return;
+        const V4 p = buf[i];
+        xr = p.x;
+        yr = p.y;
+        zr = p.z;
+        int c = 0;
+        for (int j = q; j < N; j += TPP) {
+            if (j == i) continue;
+            R dx, dy, dz;
+            const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
+            if (r2 <= k.rl2) {
+                if (c < cap) nbr[c * NT + tid] = (uint16_t)j;
+                ++c;
+            }
+        }
+        cnt = c;
+        ovf = c > cap;
+    }
+
+    __device__ bool moved(const V4* __restrict__ buf, const LJK<R>& k) const
+    {
+        if (!active) return false;
+        const V4 p = buf[i];
+        const R dx = p.x - xr, dy = p.y - yr, dz = p.z - zr;
+        return dx * dx + dy * dy + dz * dz > k.hs2;
+    }
+
+    template <typename F>
+    __device__ __forceinline__ void for_each_candidate(F&& f) const
+    {
+        if (!active) return;
+        if (!ovf) {
+            for (int m = 0; m < cnt; ++m) f((int)nbr[m * NT + tid]);
+        } else {
+            for (int j = q; j < N; j += TPP)
+                if (j != i) f(j);
+        }
+    }
+
+    __device__ __forceinline__ void group_sum(R& x, R& y, R& z) const
+    {
+#pragma unroll
+        for (int o = TPP / 2; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+    }
+
+    // F(x) of particle i (complete in every thread of the group).
+    __device__ void force(const V4* __restrict__ buf, const LJK<R>& k, R& fx, R& fy, R& fz) const
+    {
+        fx = fy = fz = R(0);
+        if (active) {
+            const V4 p = buf[i];
+            for_each_candidate([&](int j) {
+                R dx, dy, dz;
+                const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
+                if (r2 <= k.rc2) {
+                    const R ri = rsqrt_r(r2);
+                    const R ir2 = ri * ri;
+                    R s6;
+                    const R fs = force_scalar<R>(ri, ir2, k, s6);
+                    fx = fma_r(fs, dx, fx);
+                    fy = fma_r(fs, dy, fy);
+                    fz = fma_r(fs, dz, fz);
+                }
+            });
+        }
+        group_sum(fx, fy, fz);
+    }
+
+    // (H(x) v)_i with v given per particle in vbuf (own value vi).
+    __device__ void hvp(const V4* __restrict__ buf, const V4* __restrict__ vbuf, R vix, R viy,
+                        R viz, const LJK<R>& k, R& hx, R& hy, R& hz) const
+    {
+        hx = hy = hz = R(0);
+        if (active) {
+            const V4 p = buf[i];
+            for_each_candidate([&](int j) {
+                R dx, dy, dz;
+                const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
+                if (r2 <= k.rc2) {
+                    const R ri = rsqrt_r(r2);
+                    const R ir2 = ri * ri;
+                    R s6;
+                    const R A = -force_scalar<R>(ri, ir2, k, s6);     // U'(r)/r
+                    const R upp = k.e24 * ir2 * s6 * fma_r(R(26), s6, R(-7));  // U''(r)
+                    const R Bc = (upp - A) * ir2;
+                    const V4 vj = vbuf[j];
+                    const R vx = vix - vj.x, vy = viy - vj.y, vz = viz - vj.z;
+                    const R dot = fma_r(dz, vz, fma_r(dy, vy, dx * vx));
+                    const R bd = Bc * dot;
+                    hx = fma_r(A, vx, fma_r(bd, dx, hx));
+                    hy = fma_r(A, vy, fma_r(bd, dy, hy));
+                    hz = fma_r(A, vz, fma_r(bd, dz, hz));
+                }
+            });
+        }
+        group_sum(hx, hy, hz);
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ void load_slice(vec4_t<R>* buf, const R* __restrict__ Xt, int N)
+{
+    for (int n = threadIdx.x; n < N; n += blockDim.x)
+        buf[n] = make4<R>(__ldg(Xt + n), __ldg(Xt + N + n), __ldg(Xt + 2 * N + n));
+}
+
+template <typename R>
+struct LJArgs {
+    const R* pos;
+    R* grad;
+    double* partials;
+    int slot0;
+    int N, T, TS, cap;
+    long long sys_offset;
+    LJK<R> k;
+};
+
+template <typename R, int TPP, bool GRAD>
+__global__ void __launch_bounds__(1024) lj_action_kernel(const LJArgs<R> A)
+{
+    using V4 = vec4_t<R>;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const int N = A.N;
+    V4* xa = reinterpret_cast<V4*>(smem_raw);
+    V4* xb = xa + N;
+    V4* rv = xb + N;
+
+    LJBlock<R, TPP> L;
+    L.N = N;
+    L.NT = blockDim.x;
+    L.tid = threadIdx.x;
+    L.i = threadIdx.x / TPP;
+    L.q = threadIdx.x % TPP;
+    L.active = L.i < N;
+    L.cap = A.cap;
+    L.nbr = reinterpret_cast<uint16_t*>(rv + N);
+    const LJK<R>& k = A.k;
+
+    const int chain = blockIdx.y, tile = blockIdx.x;
+    const int t0 = tile * A.TS;
+    const int t1 = min(A.T, t0 + A.TS);
+    const int s = 3 * N;
+    const long long chain_len = (long long)(A.T + 1) * s;
+    const R* __restrict__ X = A.pos + A.sys_offset + chain * chain_len;
+    R* __restrict__ G = GRAD ? A.grad + A.sys_offset + chain * chain_len : nullptr;
+    const int i = L.i;
+    const bool lead = L.active && L.q == 0;
+
+    R rpx = R(0), rpy = R(0), rpz = R(0);  // r_{t-1}
+    double acc = 0.0;
+
+    // Prologue: list at the first slice the tile touches; r_{t0-1} if t0 > 0.
+    const int tf = t0 > 0 ? t0 - 1 : t0;
+    load_slice<R>(xa, X + (long long)tf * s, N);
+    __syncthreads();
+    L.build(xa, k);
+    if (t0 > 0) {
+        load_slice<R>(xb, X + (long long)t0 * s, N);
+        __syncthreads();
+        R fx, fy, fz;
+        L.force(xa, k, fx, fy, fz);
+        if (L.active) {
+            const V4 p0 = xa[i], p1 = xb[i];
+            rpx = fma_r(-k.a, fx, p1.x - p0.x);
+            rpy = fma_r(-k.a, fy, p1.y - p0.y);
+            rpz = fma_r(-k.a, fz, p1.z - p0.z);
+        }
+        __syncthreads();
+        V4* tmp = xa;
+        xa = xb;
+        xb = tmp;
+    }
+    load_slice<R>(xb, X + (long long)(t0 + 1) * s, N);
+    __syncthreads();
+
+    for (int t = t0; t < t1; ++t) {
+        // Prefetch x_{t+2} into registers while this slice is processed.
+        const bool pf = (t + 1 < t1) && (int)threadIdx.x < N;
+        R px = R(0), py = R(0), pz = R(0);
+        if (pf) {
+            const R* Xn = X + (long long)(t + 2) * s;
+            px = __ldg(Xn + threadIdx.x);
+            py = __ldg(Xn + N + threadIdx.x);
+            pz = __ldg(Xn + 2 * N + threadIdx.x);
+        }
+        if (__syncthreads_or(L.moved(xa, k))) L.build(xa, k);
+
+        R fx, fy, fz;
+        L.force(xa, k, fx, fy, fz);
+        R rx = R(0), ry = R(0), rz = R(0);
+        if (L.active) {
+            const V4 p0 = xa[i], p1 = xb[i];
+            rx = fma_r(-k.a, fx, p1.x - p0.x);
+            ry = fma_r(-k.a, fy, p1.y - p0.y);
+            rz = fma_r(-k.a, fz, p1.z - p0.z);
+            if (L.q == 0) {
+                rv[i] = make4<R>(rx, ry, rz);
+                acc += (double)fma_r(rz, rz, fma_r(ry, ry, rx * rx));
+            }
+        }
+        if (GRAD) {
+            __syncthreads();
+            R hx, hy, hz;
+            L.hvp(xa, rv, rx, ry, rz, k, hx, hy, hz);
+            if (lead) {
+                R* Gt = G + (long long)t * s;
+                Gt[i] = fma_r(k.a, hx, rpx - rx) * k.ginv;
+                Gt[N + i] = fma_r(k.a, hy, rpy - ry) * k.ginv;
+                Gt[2 * N + i] = fma_r(k.a, hz, rpz - rz) * k.ginv;
+            }
+        }
+        rpx = rx;
+        rpy = ry;
+        rpz = rz;
+        __syncthreads();
+        V4* tmp = xa;
+        xa = xb;
+        xb = tmp;
+        if (pf) xb[threadIdx.x] = make4<R>(px, py, pz);
+    }
+    if (GRAD && t1 == A.T && lead) {
+        R* Gt = G + (long long)A.T * s;
+        Gt[i] = rpx * k.ginv;
+        Gt[N + i] = rpy * k.ginv;
+        Gt[2 * N + i] = rpz * k.ginv;
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) A.partials[A.slot0 + chain * gridDim.x + tile] = tot;
+}
+
+size_t lj_smem_bytes(int N, int tpp, int maxnb, bool fp64)
+{
+    const int NT = ((N * tpp + 31) / 32) * 32;
+    const int cap = maxnb / tpp;
+    const size_t v4 = fp64 ? sizeof(double4a) : sizeof(float4);
+    return 3 * (size_t)N * v4 + (size_t)cap * NT * sizeof(uint16_t);
+}
+
+template <typename R, int TPP, bool GRAD>
+static cudaError_t launch_lj_t(const LJArgs<R>& A, int n_tiles, int n_chains, size_t smem,
+                               cudaStream_t st)
+{
+    auto kern = lj_action_kernel<R, TPP, GRAD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int NT = ((A.N * TPP + 31) / 32) * 32;
+    kern<<<dim3(n_tiles, n_chains), NT, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_lj_action(const R* pos, R* grad, double* partials, int slot0, int N, int T,
+                             int n_chains, long long sys_offset, const LJConst& c, int tile_steps,
+                             int tpp, int maxnb, bool with_grad, cudaStream_t st)
+{
+    LJArgs<R> A;
+    A.pos = pos;
+    A.grad = grad;
+    A.partials = partials;
+    A.slot0 = slot0;
+    A.N = N;
+    A.T = T;
+    A.TS = tile_steps;
+    A.cap = maxnb / tpp;
+    A.sys_offset = sys_offset;
+    A.k = make_lj_consts<R>(c, 0.0);
+    const int n_tiles = (T + tile_steps - 1) / tile_steps;
+    const size_t smem = lj_smem_bytes(N, tpp, maxnb, sizeof(R) == 8);
+    if (n_tiles <= 0 || n_chains <= 0) return cudaSuccess;
+    switch (tpp) {
+        case 1: return with_grad ? launch_lj_t<R, 1, true>(A, n_tiles, n_chains, smem, st)
+                                 : launch_lj_t<R, 1, false>(A, n_tiles, n_chains, smem, st);
+        case 2: return with_grad ? launch_lj_t<R, 2, true>(A, n_tiles, n_chains, smem, st)
+                                 : launch_lj_t<R, 2, false>(A, n_tiles, n_chains, smem, st);
+        case 4: return with_grad ? launch_lj_t<R, 4, true>(A, n_tiles, n_chains, smem, st)
+                                 : launch_lj_t<R, 4, false>(A, n_tiles, n_chains, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_lj_action<float>(const float*, float*, double*, int, int, int, int,
+                                             long long, const LJConst&, int, int, int, bool,
+                                             cudaStream_t);
+template cudaError_t launch_lj_action<double>(const double*, double*, double*, int, int, int, int,
+                                              long long, const LJConst&, int, int, int, bool,
+                                              cudaStream_t);
+
+// ------------------------------------------------------------------ Euler-Maruyama (Eq. (2))
+// One CTA per chain, sequential in time; forces as in the action kernel.
+template <typename R, int TPP>
+__global__ void __launch_bounds__(1024)
+    lj_euler_kernel(R* __restrict__ pos, const R* __restrict__ noise, int N, int T,
+                    long long sys_offset, int chain0, int cap, const LJK<R> k, uint64_t seed,
+                    uint64_t counter)
+{
+    using V4 = vec4_t<R>;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    V4* xa = reinterpret_cast<V4*>(smem_raw);
+    V4* xb = xa + N;
+    LJBlock<R, TPP> L;
+    L.N = N;
+    L.NT = blockDim.x;
+    L.tid = threadIdx.x;
+    L.i = threadIdx.x / TPP;
+    L.q = threadIdx.x % TPP;
+    L.active = L.i < N;
+    L.cap = cap;
+    L.nbr = reinterpret_cast<uint16_t*>(xb + 2 * N);  // same offset as the action kernel
+    const int chain = blockIdx.x, s = 3 * N, i = L.i;
+    const long long chain_len = (long long)(T + 1) * s;
+    R* X = pos + sys_offset + chain * chain_len;
+    const R* Z = noise ? noise + sys_offset + chain * chain_len : nullptr;
+    load_slice<R>(xa, X, N);
+    __syncthreads();
+    L.build(xa, k);
+    for (int t = 0; t < T; ++t) {
+        if (__syncthreads_or(L.moved(xa, k))) L.build(xa, k);
+        R f[3];
+        L.force(xa, k, f[0], f[1], f[2]);
+        if (L.active && L.q == 0) {
+            const V4 p = xa[i];
+            const R xo[3] = {p.x, p.y, p.z};
+            R xn[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long e = (long long)(t + 1) * s + c * N + i;
+                R z;
+                if (Z) {
+                    z = Z[e];
+                } else {
+                    const float4 w = philox_normals4(seed, counter, kStreamEuler,
+                                                     (uint32_t)(chain0 + chain), (uint32_t)(e >> 2));
+                    z = (R)pick4(w, (int)(e & 3));
+                }
+                xn[c] = xo[c] + fma_r(k.a, f[c], k.sig_em * z);
+                X[e] = xn[c];
+            }
+            xb[i] = make4<R>(xn[0], xn[1], xn[2]);
+        }
+        __syncthreads();
+        V4* tmp = xa;
+        xa = xb;
+        xb = tmp;
+    }
+}
+
+template <typename R, int TPP>
+static cudaError_t launch_lj_euler_t(R* pos, const R* noise, int N, int T, int n_chains,
+                                     long long sys_offset, int chain0, int cap, const LJK<R>& k,
+                                     uint64_t seed, uint64_t counter, size_t smem, cudaStream_t st)
+{
+    auto kern = lj_euler_kernel<R, TPP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int NT = ((N * TPP + 31) / 32) * 32;
+    kern<<<n_chains, NT, smem, st>>>(pos, noise, N, T, sys_offset, chain0, cap, k, seed, counter);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_lj_euler(R* pos, const R* noise, int N, int T, int n_chains, long long sys_offset,
+                            int chain0, const LJConst& c, int tpp, int maxnb, double sig,
+                            uint64_t seed, uint64_t counter, cudaStream_t st)
+{
+    if (n_chains <= 0 || T <= 0) return cudaSuccess;
+    const LJK<R> k = make_lj_consts<R>(c, sig);
+    const size_t smem = lj_smem_bytes(N, tpp, maxnb, sizeof(R) == 8);
+    const int cap = maxnb / tpp;
+    switch (tpp) {
+        case 1: return launch_lj_euler_t<R, 1>(pos, noise, N, T, n_chains, sys_offset, chain0, cap, k, seed, counter, smem, st);
+        case 2: return launch_lj_euler_t<R, 2>(pos, noise, N, T, n_chains, sys_offset, chain0, cap, k, seed, counter, smem, st);
+        case 4: return launch_lj_euler_t<R, 4>(pos, noise, N, T, n_chains, sys_offset, chain0, cap, k, seed, counter, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_lj_euler<float>(float*, const float*, int, int, int, long long, int,
+                                            const LJConst&, int, int, double, uint64_t, uint64_t,
+                                            cudaStream_t);
+template cudaError_t launch_lj_euler<double>(double*, const double*, int, int, int, long long, int,
+                                             const LJConst&, int, int, double, uint64_t, uint64_t,
+                                             cudaStream_t);
+
+// ------------------------------------------------------------------ pair-count diagnostic
+// Ordered in-cutoff pairs per slice, single-precision rule, all pairs.
+__global__ void __launch_bounds__(256)
+    lj_pair_count_kernel(const float* __restrict__ pos, long long* __restrict__ counts, int N, int T,
+                         long long sys_offset, const LJK<float> k)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ double red[8];
+    float4* xs = reinterpret_cast<float4*>(smem_raw);
+    const int t = blockIdx.x, chain = blockIdx.y, s = 3 * N;
+    const float* Xt = pos + sys_offset + (long long)chain * (T + 1) * s + (long long)t * s;
+    load_slice<float>(xs, Xt, N);
+    __syncthreads();
+    long long c = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float4 p = xs[i];
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            float dx, dy, dz;
+            if (pair_r2<float>(p.x, p.y, p.z, xs[j], k, dx, dy, dz) <= k.rc2) ++c;
+        }
+    }
+    const double tot = block_sum((double)c, red);
+    if (threadIdx.x == 0) counts[(long long)chain * (T + 1) + t] = (long long)tot;
+}
+
+cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, int T, int n_chains,
+                                  long long sys_offset, double L, double rc, cudaStream_t st)
+{
+    LJConst c{};
+    c.L = L;
+    c.rc = rc;
+    c.eps = 1.0;
+    c.sigma = 1.0;
+    const LJK<float> k = make_lj_consts<float>(c, 0.0);
+    const size_t smem = (size_t)N * sizeof(float4);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(lj_pair_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    lj_pair_count_kernel<<<dim3(T + 1, n_chains), 256, smem, st>>>(pos, counts, N, T, sys_offset, k);
+    return cudaGetLastError();
+}
+
+}  // namespace pamd

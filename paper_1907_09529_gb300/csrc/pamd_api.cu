@@ -1,0 +1,711 @@
+// pamd_api.cu -- the C ABI of libpamd: argument checks, cached plans (work
+// descriptors, workspace, captured graphs), host-buffer staging, dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "pamd_internal.cuh"
+
+using namespace pamd;
+
+namespace {
+
+#define PAMD_CUDA_TRY(expr)                           \
+    do {                                              \
+        cudaError_t _e = (expr);                      \
+        if (_e != cudaSuccess) return PAMD_ERR_CUDA;  \
+    } while (0)
+
+struct LJTune {
+    int tile_steps = 0, tpp = 0, maxnb = 0;
+    double skin = -1.0;
+};
+
+LJTune g_tune_override;  // 0 / negative fields mean "automatic"
+std::mutex g_mutex;
+
+struct SysInfo {
+    int N, T, d, chains, kind, chain0;
+    long long off, chain_len;
+    pamd_potential pot;
+    LJTune tune;       // LJ only
+    int slot0 = 0;     // first S slot (LJ tiles)
+    int n_tiles = 0;
+};
+
+struct GraphKey {
+    const void *pos, *grad, *S, *nacc, *la;
+    int n_updates;
+    bool operator<(const GraphKey& o) const
+    {
+        return std::memcmp(this, &o, sizeof(GraphKey)) < 0;
+    }
+};
+
+struct Plan {
+    std::string key;
+    bool fp64 = false;
+    int n_chains = 0;
+    size_t esz = 4;
+    long long span = 0;  // elements spanned by the pos buffer
+    std::vector<SysInfo> sys;
+    std::vector<ElemBlock> h_all, h_ho;
+    std::vector<int> ho_chain_first;  // per chain: first HO block index (or -1), and count
+    std::vector<int> ho_chain_count;
+    int max_s_ho = 0;
+    ElemBlock* d_all = nullptr;
+    ElemBlock* d_ho = nullptr;
+    ChainSlots* d_S_slots = nullptr;
+    ChainSlots* d_E_slots = nullptr;
+    int n_S_slots = 0;
+    double* d_part_S = nullptr;
+    double* d_part_qf = nullptr;
+    double* d_part_qr = nullptr;
+    // update workspace (allocated on first use)
+    void* d_prop = nullptr;
+    void* d_gprop = nullptr;
+    double* d_Sprop = nullptr;
+    double* d_qf = nullptr;
+    double* d_qr = nullptr;
+    int* d_flag = nullptr;
+    MalaDev* d_md = nullptr;
+    // host-pointer staging (allocated on first use)
+    void* d_stage_pos = nullptr;
+    void* d_stage_grad = nullptr;
+    void* d_stage_noise = nullptr;
+    double* d_stage_S = nullptr;
+    double* d_stage_dbl = nullptr;  // log_alpha
+    double* d_stage_logu = nullptr;
+    int* d_stage_int = nullptr;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::vector<void*> allocs;
+
+    ~Plan()
+    {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        for (void* p : allocs) cudaFree(p);
+    }
+    template <typename T>
+    int alloc(T** p, size_t bytes)
+    {
+        void* q = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) return PAMD_ERR_ALLOC;
+        allocs.push_back(q);
+        *p = reinterpret_cast<T*>(q);
+        return PAMD_OK;
+    }
+};
+
+std::map<std::string, std::unique_ptr<Plan>> g_plans;
+
+int check_problem(const pamd_problem* p)
+{
+    if (!p || !p->systems || p->n_systems <= 0) return PAMD_ERR_ARG;
+    if (p->precision != PAMD_FP32 && p->precision != PAMD_FP64) return PAMD_ERR_ARG;
+    if (!(p->D > 0) || !(p->dt > 0) || !(p->beta > 0)) return PAMD_ERR_ARG;
+    for (int q = 0; q < p->n_systems; ++q) {
+        const pamd_system& s = p->systems[q];
+        if (s.n_particles < 1 || s.n_steps < 1 || s.dim < 1 || s.dim > 3 || s.n_chains < 1 ||
+            s.pos_offset < 0)
+            return PAMD_ERR_ARG;
+        const long long chain_len = (long long)(s.n_steps + 1) * s.dim * s.n_particles;
+        if (chain_len >= (1LL << 31)) return PAMD_ERR_UNSUPPORTED;
+        if (s.pot.kind == PAMD_HARMONIC) {
+            if (s.dim * s.n_particles > 8192) return PAMD_ERR_UNSUPPORTED;
+        } else if (s.pot.kind == PAMD_LJ) {
+            if (s.dim != 3 || s.n_particles < 2) return PAMD_ERR_ARG;
+            if (s.n_particles > 1024) return PAMD_ERR_UNSUPPORTED;
+            if (!(s.pot.box > 0) || !(s.pot.rc > 0) || s.pot.rc > 0.5 * s.pot.box ||
+                !(s.pot.sigma > 0) || !(s.pot.eps >= 0))
+                return PAMD_ERR_ARG;
+        } else {
+            return PAMD_ERR_ARG;
+        }
+    }
+    return PAMD_OK;
+}
+
+std::string plan_key(const pamd_problem* p)
+{
+    std::ostringstream os;
+    os.precision(17);
+    os << p->precision << '|' << p->flags << '|' << p->n_systems << '|' << g_tune_override.tile_steps
+       << ',' << g_tune_override.tpp << ',' << g_tune_override.maxnb << ',' << g_tune_override.skin;
+    for (int q = 0; q < p->n_systems; ++q) {
+        const pamd_system& s = p->systems[q];
+        os << '|' << s.n_particles << ',' << s.n_steps << ',' << s.dim << ',' << s.n_chains << ','
+           << s.pos_offset << ',' << s.pot.kind << ',' << s.pot.k << ',' << s.pot.eps << ','
+           << s.pot.sigma << ',' << s.pot.rc << ',' << s.pot.box;
+    }
+    return os.str();
+}
+
+int max_dynamic_smem()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 48 * 1024;
+    return v;
+}
+
+// Default LJ launch shape: threads per particle, Verlet skin, list capacity, tile.
+LJTune choose_lj_tune(const pamd_system& s, bool fp64)
+{
+    LJTune t;
+    const int N = s.n_particles;
+    t.tpp = g_tune_override.tpp > 0 ? g_tune_override.tpp : (N <= 256 ? 4 : (N <= 512 ? 2 : 1));
+    while (t.tpp > 1 && N * t.tpp > 1024) t.tpp >>= 1;
+    t.skin = g_tune_override.skin >= 0 ? g_tune_override.skin : 0.25;
+    t.tile_steps = g_tune_override.tile_steps > 0 ? g_tune_override.tile_steps : 32;
+    const double L = s.pot.box, rho = N / (L * L * L), rl = s.pot.rc + t.skin;
+    const double expect = 4.18879020478639 * rl * rl * rl * rho;  // 4/3 pi rl^3 rho
+    int want = (int)(1.3 * expect) + 16;
+    if (want > N - 1 + t.tpp) want = N - 1 + t.tpp;
+    if (g_tune_override.maxnb > 0) want = g_tune_override.maxnb;
+    want = ((want + t.tpp - 1) / t.tpp) * t.tpp;
+    // shrink until it fits in shared memory
+    const int smax = max_dynamic_smem() - 1024;
+    while (want > t.tpp && (int)lj_smem_bytes(N, t.tpp, want, fp64) > smax) want -= t.tpp;
+    t.maxnb = want;
+    return t;
+}
+
+int build_plan(const pamd_problem* p, Plan** out)
+{
+    std::string key = plan_key(p);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+        *out = it->second.get();
+        return PAMD_OK;
+    }
+    std::unique_ptr<Plan> P(new Plan());
+    P->key = key;
+    P->fp64 = p->precision == PAMD_FP64;
+    P->esz = P->fp64 ? 8 : 4;
+    int chain = 0;
+    std::vector<ChainSlots> Sslots, Eslots;
+    for (int q = 0; q < p->n_systems; ++q) {
+        const pamd_system& s = p->systems[q];
+        SysInfo si;
+        si.N = s.n_particles;
+        si.T = s.n_steps;
+        si.d = s.dim;
+        si.chains = s.n_chains;
+        si.kind = s.pot.kind;
+        si.chain0 = chain;
+        si.off = s.pos_offset;
+        si.chain_len = (long long)(s.n_steps + 1) * s.dim * s.n_particles;
+        si.pot = s.pot;
+        if (si.kind == PAMD_LJ) si.tune = choose_lj_tune(s, P->fp64);
+        P->span = std::max(P->span, si.off + si.chain_len * si.chains);
+        P->sys.push_back(si);
+        chain += s.n_chains;
+    }
+    P->n_chains = chain;
+    Sslots.resize(chain);
+    Eslots.resize(chain);
+    P->ho_chain_first.assign(chain, -1);
+    P->ho_chain_count.assign(chain, 0);
+    // element blocks: all systems (update passes) and harmonic systems (action)
+    for (auto& si : P->sys) {
+        const int s = si.d * si.N;
+        for (int b = 0; b < si.chains; ++b) {
+            const int c = si.chain0 + b;
+            Eslots[c].begin = (int)P->h_all.size();
+            if (si.kind == PAMD_HARMONIC) {
+                Sslots[c].begin = (int)P->h_ho.size();
+                P->ho_chain_first[c] = (int)P->h_ho.size();
+            }
+            for (long long e0 = 0; e0 < si.chain_len; e0 += kElemChunk) {
+                ElemBlock B;
+                B.chain_base = si.off + b * si.chain_len;
+                B.e0 = (int)e0;
+                B.n = (int)std::min<long long>(kElemChunk, si.chain_len - e0);
+                B.s = s;
+                B.chain_len = (int)si.chain_len;
+                B.chain = c;
+                B.sys = (int)(&si - &P->sys[0]);
+                B.k = si.pot.k;
+                P->h_all.push_back(B);
+                if (si.kind == PAMD_HARMONIC) P->h_ho.push_back(B);
+            }
+            Eslots[c].end = (int)P->h_all.size();
+            if (si.kind == PAMD_HARMONIC) {
+                Sslots[c].end = (int)P->h_ho.size();
+                P->ho_chain_count[c] = Sslots[c].end - Sslots[c].begin;
+                P->max_s_ho = std::max(P->max_s_ho, s);
+            }
+        }
+    }
+    int slot = (int)P->h_ho.size();
+    for (auto& si : P->sys) {
+        if (si.kind != PAMD_LJ) continue;
+        si.n_tiles = (si.T + si.tune.tile_steps - 1) / si.tune.tile_steps;
+        si.slot0 = slot;
+        for (int b = 0; b < si.chains; ++b) {
+            Sslots[si.chain0 + b].begin = slot + b * si.n_tiles;
+            Sslots[si.chain0 + b].end = slot + (b + 1) * si.n_tiles;
+        }
+        slot += si.chains * si.n_tiles;
+    }
+    P->n_S_slots = slot;
+    int rc;
+    if ((rc = P->alloc(&P->d_all, sizeof(ElemBlock) * P->h_all.size()))) return rc;
+    if ((rc = P->alloc(&P->d_ho, sizeof(ElemBlock) * P->h_ho.size()))) return rc;
+    if ((rc = P->alloc(&P->d_S_slots, sizeof(ChainSlots) * chain))) return rc;
+    if ((rc = P->alloc(&P->d_E_slots, sizeof(ChainSlots) * chain))) return rc;
+    if ((rc = P->alloc(&P->d_part_S, sizeof(double) * P->n_S_slots))) return rc;
+    if ((rc = P->alloc(&P->d_part_qf, sizeof(double) * P->h_all.size()))) return rc;
+    if ((rc = P->alloc(&P->d_part_qr, sizeof(double) * P->h_all.size()))) return rc;
+    if (!P->h_all.empty())
+        PAMD_CUDA_TRY(cudaMemcpy(P->d_all, P->h_all.data(), sizeof(ElemBlock) * P->h_all.size(),
+                                 cudaMemcpyHostToDevice));
+    if (!P->h_ho.empty())
+        PAMD_CUDA_TRY(cudaMemcpy(P->d_ho, P->h_ho.data(), sizeof(ElemBlock) * P->h_ho.size(),
+                                 cudaMemcpyHostToDevice));
+    PAMD_CUDA_TRY(cudaMemcpy(P->d_S_slots, Sslots.data(), sizeof(ChainSlots) * chain,
+                             cudaMemcpyHostToDevice));
+    PAMD_CUDA_TRY(cudaMemcpy(P->d_E_slots, Eslots.data(), sizeof(ChainSlots) * chain,
+                             cudaMemcpyHostToDevice));
+    *out = P.get();
+    g_plans[key] = std::move(P);
+    return PAMD_OK;
+}
+
+int ensure_update_ws(Plan* P)
+{
+    if (P->d_prop) return PAMD_OK;
+    int rc;
+    if ((rc = P->alloc(&P->d_prop, P->esz * (size_t)P->span))) return rc;
+    if ((rc = P->alloc(&P->d_gprop, P->esz * (size_t)P->span))) return rc;
+    if ((rc = P->alloc(&P->d_Sprop, sizeof(double) * P->n_chains))) return rc;
+    if ((rc = P->alloc(&P->d_qf, sizeof(double) * P->n_chains))) return rc;
+    if ((rc = P->alloc(&P->d_qr, sizeof(double) * P->n_chains))) return rc;
+    if ((rc = P->alloc(&P->d_flag, sizeof(int) * P->n_chains))) return rc;
+    if ((rc = P->alloc(&P->d_md, sizeof(MalaDev)))) return rc;
+    PAMD_CUDA_TRY(cudaMemset(P->d_prop, 0, P->esz * (size_t)P->span));
+    PAMD_CUDA_TRY(cudaMemset(P->d_gprop, 0, P->esz * (size_t)P->span));
+    return PAMD_OK;
+}
+
+bool is_host_ptr(const void* ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+}
+
+LJConst lj_const(const pamd_problem* p, const SysInfo& si)
+{
+    LJConst c;
+    c.L = si.pot.box;
+    c.rc = si.pot.rc;
+    c.eps = si.pot.eps;
+    c.sigma = si.pot.sigma;
+    c.a = p->beta * p->D * p->dt;
+    c.ginv = 1.0 / (2.0 * p->D * p->dt);
+    c.skin = si.tune.skin;
+    return c;
+}
+
+// S (and grad) of every chain into S_out, from device pointers.
+template <typename R>
+int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_out, bool with_grad,
+               cudaStream_t st)
+{
+    const double a = p->beta * p->D * p->dt, ginv = 1.0 / (2.0 * p->D * p->dt);
+    const bool one = (p->flags & PAMD_FLAG_ONE_CHAIN_PER_LAUNCH) != 0;
+    if (!P->h_ho.empty()) {
+        if (!one) {
+            PAMD_CUDA_TRY(launch_ho_action<R>(P->d_ho, (int)P->h_ho.size(), P->max_s_ho, pos, grad,
+                                              P->d_part_S, 0, a, ginv, with_grad, st));
+        } else {
+            for (int c = 0; c < P->n_chains; ++c) {
+                const int f = P->ho_chain_first[c];
+                if (f < 0) continue;
+                PAMD_CUDA_TRY(launch_ho_action<R>(P->d_ho + f, P->ho_chain_count[c], P->max_s_ho, pos,
+                                                  grad, P->d_part_S, f, a, ginv, with_grad, st));
+            }
+        }
+    }
+    for (const auto& si : P->sys) {
+        if (si.kind != PAMD_LJ) continue;
+        const LJConst c = lj_const(p, si);
+        if (!one) {
+            PAMD_CUDA_TRY(launch_lj_action<R>(pos, grad, P->d_part_S, si.slot0, si.N, si.T, si.chains,
+                                              si.off, c, si.tune.tile_steps, si.tune.tpp,
+                                              si.tune.maxnb, with_grad, st));
+        } else {
+            for (int b = 0; b < si.chains; ++b)
+                PAMD_CUDA_TRY(launch_lj_action<R>(pos, grad, P->d_part_S, si.slot0 + b * si.n_tiles,
+                                                  si.N, si.T, 1, si.off + b * si.chain_len, c,
+                                                  si.tune.tile_steps, si.tune.tpp, si.tune.maxnb,
+                                                  with_grad, st));
+        }
+    }
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_S, P->d_S_slots, P->n_chains, 1.0 / (4.0 * p->D * p->dt),
+                                  S_out, st));
+    return PAMD_OK;
+}
+
+template <typename R>
+int run_one_update(const pamd_problem* p, Plan* P, R* pos, R* grad, double* S, const R* noise,
+                   const double* log_u, int* n_acc, double* la, int u, cudaStream_t st)
+{
+    const int nb = (int)P->h_all.size();
+    R* prop = reinterpret_cast<R*>(P->d_prop);
+    R* gprop = reinterpret_cast<R*>(P->d_gprop);
+    PAMD_CUDA_TRY(launch_mala_propose<R>(P->d_all, nb, pos, grad, noise, prop, P->d_part_qf, P->d_md,
+                                         u, st));
+    int rc = run_action<R>(p, P, prop, gprop, P->d_Sprop, true, st);
+    if (rc) return rc;
+    PAMD_CUDA_TRY(launch_mala_reverse<R>(P->d_all, nb, pos, prop, gprop, P->d_part_qr, P->d_md, st));
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_qf, P->d_E_slots, P->n_chains, 1.0, P->d_qf, st));
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_qr, P->d_E_slots, P->n_chains, 1.0, P->d_qr, st));
+    PAMD_CUDA_TRY(launch_mala_accept(P->n_chains, S, P->d_Sprop, P->d_qf, P->d_qr, log_u, P->d_md, u,
+                                     P->d_flag, n_acc, la, st));
+    PAMD_CUDA_TRY(launch_mala_commit<R>(P->d_all, nb, pos, grad, prop, gprop, P->d_flag, S, P->d_Sprop,
+                                        st));
+    return PAMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pamd_version(void) { return 1; }
+
+const char* pamd_status_string(int status)
+{
+    switch (status) {
+        case PAMD_OK: return "ok";
+        case PAMD_ERR_ARG: return "invalid argument";
+        case PAMD_ERR_UNSUPPORTED: return "unsupported shape";
+        case PAMD_ERR_CUDA: return "CUDA error";
+        case PAMD_ERR_TIMEOUT: return "device wait timed out";
+        case PAMD_ERR_NONFINITE: return "non-finite action";
+        case PAMD_ERR_ALLOC: return "workspace allocation failed";
+        default: return "unknown status";
+    }
+}
+
+int pamd_release_cache(void)
+{
+    std::lock_guard<std::mutex> lk(g_mutex);
+    cudaDeviceSynchronize();
+    g_plans.clear();
+    return PAMD_OK;
+}
+
+int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin)
+{
+    if (threads_per_particle != 0 && threads_per_particle != 1 && threads_per_particle != 2 &&
+        threads_per_particle != 4)
+        return PAMD_ERR_ARG;
+    if (tile_steps < 0 || max_neighbours < 0) return PAMD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    g_tune_override.tile_steps = tile_steps;
+    g_tune_override.tpp = threads_per_particle;
+    g_tune_override.maxnb = max_neighbours;
+    g_tune_override.skin = skin;
+    return PAMD_OK;
+}
+
+static int action_common(const pamd_problem* prob, const void* pos, double* S, void* grad,
+                         bool with_grad, void* stream)
+{
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!pos || !S || (with_grad && !grad)) return PAMD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    if ((rc = build_plan(prob, &P))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool host = is_host_ptr(pos) || is_host_ptr(S) || (with_grad && is_host_ptr(grad));
+    const void* dpos = pos;
+    void* dgrad = grad;
+    double* dS = S;
+    const size_t bytes = P->esz * (size_t)P->span;
+    if (host) {
+        if (!P->d_stage_pos && (rc = P->alloc(&P->d_stage_pos, bytes))) return rc;
+        if (with_grad && !P->d_stage_grad && (rc = P->alloc(&P->d_stage_grad, bytes))) return rc;
+        if (!P->d_stage_S && (rc = P->alloc(&P->d_stage_S, sizeof(double) * P->n_chains))) return rc;
+        if (is_host_ptr(pos)) {
+            PAMD_CUDA_TRY(cudaMemcpyAsync(P->d_stage_pos, pos, bytes, cudaMemcpyHostToDevice, st));
+            dpos = P->d_stage_pos;
+        }
+        if (with_grad && is_host_ptr(grad)) dgrad = P->d_stage_grad;
+        if (is_host_ptr(S)) dS = P->d_stage_S;
+    }
+    if (P->fp64)
+        rc = run_action<double>(prob, P, (const double*)dpos, (double*)dgrad, dS, with_grad, st);
+    else
+        rc = run_action<float>(prob, P, (const float*)dpos, (float*)dgrad, dS, with_grad, st);
+    if (rc) return rc;
+    if (host) {
+        if (with_grad && dgrad != grad)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(grad, dgrad, bytes, cudaMemcpyDeviceToHost, st));
+        if (dS != S)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(S, dS, sizeof(double) * P->n_chains, cudaMemcpyDeviceToHost, st));
+        PAMD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return PAMD_OK;
+}
+
+int pamd_action(const pamd_problem* prob, const void* pos, double* S, void* stream)
+{
+    return action_common(prob, pos, S, nullptr, false, stream);
+}
+
+int pamd_action_grad(const pamd_problem* prob, const void* pos, double* S, void* grad, void* stream)
+{
+    return action_common(prob, pos, S, grad, true, stream);
+}
+
+int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S, double h,
+                     int n_updates, uint64_t seed, uint64_t counter, const void* noise,
+                     const double* log_u, int* n_accepted, double* log_alpha, void* stream)
+{
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!pos || !grad || !S || !(h > 0) || n_updates < 0) return PAMD_ERR_ARG;
+    if ((noise || log_u) && n_updates != 1) return PAMD_ERR_ARG;
+    if (n_updates == 0) return PAMD_OK;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    if ((rc = build_plan(prob, &P))) return rc;
+    if ((rc = ensure_update_ws(P))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = P->esz * (size_t)P->span;
+    const size_t nc = (size_t)P->n_chains;
+    const bool host = is_host_ptr(pos) || is_host_ptr(grad) || is_host_ptr(S) ||
+                      is_host_ptr(noise) || is_host_ptr(log_u) || is_host_ptr(n_accepted) ||
+                      is_host_ptr(log_alpha);
+    void *dpos = pos, *dgrad = grad;
+    double* dS = S;
+    const void* dnoise = noise;
+    const double* dlogu = log_u;
+    int* dnacc = n_accepted;
+    double* dla = log_alpha;
+    if (host) {
+        if (!P->d_stage_pos && (rc = P->alloc(&P->d_stage_pos, bytes))) return rc;
+        if (!P->d_stage_grad && (rc = P->alloc(&P->d_stage_grad, bytes))) return rc;
+        if (!P->d_stage_S && (rc = P->alloc(&P->d_stage_S, sizeof(double) * nc))) return rc;
+        if (!P->d_stage_dbl && (rc = P->alloc(&P->d_stage_dbl, sizeof(double) * nc))) return rc;
+        if (!P->d_stage_logu && (rc = P->alloc(&P->d_stage_logu, sizeof(double) * nc))) return rc;
+        if (!P->d_stage_int && (rc = P->alloc(&P->d_stage_int, sizeof(int) * nc))) return rc;
+        if (noise && !P->d_stage_noise && (rc = P->alloc(&P->d_stage_noise, bytes))) return rc;
+        if (is_host_ptr(pos)) {
+            dpos = P->d_stage_pos;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(dpos, pos, bytes, cudaMemcpyHostToDevice, st));
+        }
+        if (is_host_ptr(grad)) {
+            dgrad = P->d_stage_grad;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(dgrad, grad, bytes, cudaMemcpyHostToDevice, st));
+        }
+        if (is_host_ptr(S)) {
+            dS = P->d_stage_S;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(dS, S, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+        }
+        if (noise && is_host_ptr(noise)) {
+            dnoise = P->d_stage_noise;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(P->d_stage_noise, noise, bytes, cudaMemcpyHostToDevice, st));
+        }
+        if (log_u && is_host_ptr(log_u)) {
+            dlogu = P->d_stage_logu;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(P->d_stage_logu, log_u, sizeof(double) * nc,
+                                          cudaMemcpyHostToDevice, st));
+        }
+        if (n_accepted && is_host_ptr(n_accepted)) {
+            dnacc = P->d_stage_int;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(dnacc, n_accepted, sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+        }
+        if (log_alpha && is_host_ptr(log_alpha)) dla = P->d_stage_dbl;
+    }
+    PAMD_CUDA_TRY(launch_set_mala_params(P->d_md, seed, counter, h, st));
+    const bool use_graph = !host && n_updates > 1;
+    if (!use_graph) {
+        for (int u = 0; u < n_updates; ++u) {
+            rc = P->fp64 ? run_one_update<double>(prob, P, (double*)dpos, (double*)dgrad, dS,
+                                                  (const double*)dnoise, dlogu, dnacc, dla, u, st)
+                         : run_one_update<float>(prob, P, (float*)dpos, (float*)dgrad, dS,
+                                                 (const float*)dnoise, dlogu, dnacc, dla, u, st);
+            if (rc) return rc;
+        }
+    } else {
+        GraphKey gk{dpos, dgrad, dS, dnacc, dla, n_updates};
+        auto it = P->graphs.find(gk);
+        if (it == P->graphs.end()) {
+            cudaStream_t cap;
+            PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                cudaStreamDestroy(cap);
+                return PAMD_ERR_CUDA;
+            }
+            for (int u = 0; u < n_updates && !rc; ++u)
+                rc = P->fp64 ? run_one_update<double>(prob, P, (double*)dpos, (double*)dgrad, dS,
+                                                      nullptr, nullptr, dnacc, dla, u, cap)
+                             : run_one_update<float>(prob, P, (float*)dpos, (float*)dgrad, dS,
+                                                     nullptr, nullptr, dnacc, dla, u, cap);
+            cudaError_t ce = cudaStreamEndCapture(cap, &g);
+            cudaStreamDestroy(cap);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ce != cudaSuccess) return PAMD_ERR_CUDA;
+            cudaGraphExec_t ex;
+            ce = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return PAMD_ERR_CUDA;
+            it = P->graphs.emplace(gk, ex).first;
+        }
+        PAMD_CUDA_TRY(cudaGraphLaunch(it->second, st));
+    }
+    if (host) {
+        if (dpos != pos) PAMD_CUDA_TRY(cudaMemcpyAsync(pos, dpos, bytes, cudaMemcpyDeviceToHost, st));
+        if (dgrad != grad) PAMD_CUDA_TRY(cudaMemcpyAsync(grad, dgrad, bytes, cudaMemcpyDeviceToHost, st));
+        if (dS != S) PAMD_CUDA_TRY(cudaMemcpyAsync(S, dS, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
+        if (dnacc != n_accepted)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(n_accepted, dnacc, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+        if (dla != log_alpha)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(log_alpha, dla, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
+        PAMD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return PAMD_OK;
+}
+
+int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uint64_t counter,
+                         const void* noise, void* stream)
+{
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!pos) return PAMD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    if ((rc = build_plan(prob, &P))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = P->esz * (size_t)P->span;
+    const bool host = is_host_ptr(pos) || is_host_ptr(noise);
+    void* dpos = pos;
+    const void* dnoise = noise;
+    if (host) {
+        if (!P->d_stage_pos && (rc = P->alloc(&P->d_stage_pos, bytes))) return rc;
+        if (noise && !P->d_stage_noise && (rc = P->alloc(&P->d_stage_noise, bytes))) return rc;
+        if (is_host_ptr(pos)) {
+            dpos = P->d_stage_pos;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(dpos, pos, bytes, cudaMemcpyHostToDevice, st));
+        }
+        if (noise && is_host_ptr(noise)) {
+            dnoise = P->d_stage_noise;
+            PAMD_CUDA_TRY(cudaMemcpyAsync(P->d_stage_noise, noise, bytes, cudaMemcpyHostToDevice, st));
+        }
+    }
+    const double a = prob->beta * prob->D * prob->dt, sig = std::sqrt(2.0 * prob->D * prob->dt);
+    for (const auto& si : P->sys) {
+        if (si.kind == PAMD_HARMONIC) {
+            if (P->fp64)
+                PAMD_CUDA_TRY(launch_ho_euler<double>((double*)dpos, (const double*)dnoise, si.d * si.N,
+                                                      si.T, si.chains, si.off, si.chain0, si.pot.k, a,
+                                                      sig, seed, counter, st));
+            else
+                PAMD_CUDA_TRY(launch_ho_euler<float>((float*)dpos, (const float*)dnoise, si.d * si.N,
+                                                     si.T, si.chains, si.off, si.chain0, si.pot.k, a,
+                                                     sig, seed, counter, st));
+        } else {
+            const LJConst c = lj_const(prob, si);
+            if (P->fp64)
+                PAMD_CUDA_TRY(launch_lj_euler<double>((double*)dpos, (const double*)dnoise, si.N, si.T,
+                                                      si.chains, si.off, si.chain0, c, si.tune.tpp,
+                                                      si.tune.maxnb, sig, seed, counter, st));
+            else
+                PAMD_CUDA_TRY(launch_lj_euler<float>((float*)dpos, (const float*)dnoise, si.N, si.T,
+                                                     si.chains, si.off, si.chain0, c, si.tune.tpp,
+                                                     si.tune.maxnb, sig, seed, counter, st));
+        }
+    }
+    if (host) {
+        if (dpos != pos) PAMD_CUDA_TRY(cudaMemcpyAsync(pos, dpos, bytes, cudaMemcpyDeviceToHost, st));
+        PAMD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return PAMD_OK;
+}
+
+int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* counts, void* stream)
+{
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!pos || !counts || prob->precision != PAMD_FP32) return PAMD_ERR_ARG;
+    if (is_host_ptr(pos) || is_host_ptr(counts)) return PAMD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long out_off = 0;
+    for (int q = 0; q < prob->n_systems; ++q) {
+        const pamd_system& s = prob->systems[q];
+        if (s.pot.kind != PAMD_LJ) continue;
+        PAMD_CUDA_TRY(launch_lj_pair_counts((const float*)pos, counts + out_off, s.n_particles,
+                                            s.n_steps, s.n_chains, s.pos_offset, s.pot.box, s.pot.rc,
+                                            st));
+        out_off += (long long)s.n_chains * (s.n_steps + 1);
+    }
+    return PAMD_OK;
+}
+
+int pamd_philox(uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3, uint32_t key0,
+                uint32_t key1, long long n, uint32_t* out, void* stream)
+{
+    if (n < 0 || !out) return PAMD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_host_ptr(out)) {
+        uint32_t* d = nullptr;
+        if (cudaMalloc(&d, sizeof(uint32_t) * 4 * (size_t)std::max(n, 1LL)) != cudaSuccess)
+            return PAMD_ERR_ALLOC;
+        int rc = launch_philox(make_uint4(ctr0, ctr1, ctr2, ctr3), make_uint2(key0, key1), n, d, st) ==
+                         cudaSuccess
+                     ? PAMD_OK
+                     : PAMD_ERR_CUDA;
+        if (!rc && cudaMemcpyAsync(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = PAMD_ERR_CUDA;
+        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = PAMD_ERR_CUDA;
+        cudaFree(d);
+        return rc;
+    }
+    PAMD_CUDA_TRY(launch_philox(make_uint4(ctr0, ctr1, ctr2, ctr3), make_uint2(key0, key1), n, out, st));
+    return PAMD_OK;
+}
+
+int pamd_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain, long long e0,
+                 long long n, float* out, void* stream)
+{
+    if (n < 0 || e0 < 0 || !out) return PAMD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_host_ptr(out)) {
+        float* d = nullptr;
+        if (cudaMalloc(&d, sizeof(float) * (size_t)std::max(n, 1LL)) != cudaSuccess) return PAMD_ERR_ALLOC;
+        int rc = launch_normals(seed, counter, stream_id, chain, e0, n, d, st) == cudaSuccess ? PAMD_OK
+                                                                                               : PAMD_ERR_CUDA;
+        if (!rc && cudaMemcpyAsync(out, d, sizeof(float) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = PAMD_ERR_CUDA;
+        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = PAMD_ERR_CUDA;
+        cudaFree(d);
+        return rc;
+    }
+    PAMD_CUDA_TRY(launch_normals(seed, counter, stream_id, chain, e0, n, out, st));
+    return PAMD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,222 @@
+// pamd_internal.cuh -- device helpers and kernel argument blocks shared by the
+// libpamd translation units.  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pamd.h"
+
+namespace pamd {
+
+// ------------------------------------------------------------------ vector types
+struct alignas(32) double4a {
+    double x, y, z, w;
+};
+template <typename R>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+template <>
+struct Vec4<double> {
+    using type = double4a;
+};
+template <typename R>
+using vec4_t = typename Vec4<R>::type;
+
+template <typename R>
+__device__ __forceinline__ vec4_t<R> make4(R x, R y, R z)
+{
+    vec4_t<R> v;
+    v.x = x;
+    v.y = y;
+    v.z = z;
+    v.w = R(0);
+    return v;
+}
+
+// Round-to-nearest-integer and fused multiply-add in the element type.
+__device__ __forceinline__ float rint_r(float v) { return rintf(v); }
+__device__ __forceinline__ double rint_r(double v) { return rint(v); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds; each round multiplies words 0 and 2 by two odd 32-bit
+// constants, mixes the high halves with words 1/3 and the round key; the key
+// is advanced by two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Four standard normals for element group `group` (elements 4*group..4*group+3)
+// of one chain's noise stream: 24-bit uniforms, Box-Muller in single precision.
+__device__ __forceinline__ float4 philox_normals4(uint64_t seed, uint64_t counter, uint32_t stream,
+                                                  uint32_t chain, uint32_t group)
+{
+    const uint4 ctr = make_uint4(group, chain, (uint32_t)counter,
+                                 (uint32_t)((counter >> 32) & 0xFFFFu) | (stream << 16));
+    const uint4 w = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const float two_m24 = 5.9604644775390625e-8f;  // 2^-24
+    const float u0 = (float)((w.x >> 8) + 1u) * two_m24;
+    const float v1 = (float)(w.y >> 8) * two_m24;
+    const float u2 = (float)((w.z >> 8) + 1u) * two_m24;
+    const float v3 = (float)(w.w >> 8) * two_m24;
+    const float ra = sqrtf(-2.0f * logf(u0));
+    const float rb = sqrtf(-2.0f * logf(u2));
+    float sa, ca, sb, cb;
+    sincospif(2.0f * v1, &sa, &ca);
+    sincospif(2.0f * v3, &sb, &cb);
+    return make_float4(ra * ca, ra * sa, rb * cb, rb * sb);
+}
+
+__device__ __forceinline__ float pick4(const float4& v, int lane)
+{
+    return lane == 0 ? v.x : lane == 1 ? v.y : lane == 2 ? v.z : v.w;
+}
+
+// Uniform in (0,1] with 53 bits (words 0 and 1), for the per-chain accept test.
+__device__ __forceinline__ double philox_uniform53(uint64_t seed, uint64_t counter, uint32_t stream,
+                                                   uint32_t chain)
+{
+    const uint4 ctr = make_uint4(0u, chain, (uint32_t)counter,
+                                 (uint32_t)((counter >> 32) & 0xFFFFu) | (stream << 16));
+    const uint4 w = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint64_t m = (uint64_t)(w.x >> 5) * 67108864ull + (uint64_t)(w.y >> 6);
+    return ((double)m + 1.0) * 1.1102230246251565e-16;  // 2^-53
+}
+
+enum : uint32_t { kStreamEuler = 0, kStreamMala = 1, kStreamAccept = 2 };
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed tree); result valid in thread 0.
+// `scratch` needs blockDim.x/32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* scratch)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        for (int q = lane; q < nw; q += 32) s += scratch[q];
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ work descriptors
+// A contiguous run of elements of one chain (element-wise passes).
+struct ElemBlock {
+    long long chain_base;  // element offset of the chain's slice 0 in the buffer
+    int e0;                // first chain-local element handled by this block
+    int n;                 // number of elements
+    int s;                 // elements per slice (dim * N)
+    int chain_len;         // (T+1) * s
+    int chain;             // global chain index
+    int sys;               // system index
+    double k;              // harmonic constant (harmonic systems)
+};
+
+constexpr int kElemThreads = 256;
+constexpr int kElemChunk = 4096;  // elements per ElemBlock
+
+// Slot ranges of one chain in a partial-sum array.
+struct ChainSlots {
+    int begin, end;
+};
+
+// ------------------------------------------------------------------ launchers
+// Harmonic action (+ gradient) over element blocks.  Writes one partial
+// sum of |r|^2 per block into partials[slot0 + block].
+template <typename R>
+cudaError_t launch_ho_action(const ElemBlock* blocks, int n_blocks, int max_s, const R* pos, R* grad,
+                             double* partials, int slot0, double a, double ginv, bool with_grad,
+                             cudaStream_t st);
+
+struct LJConst {
+    double L, rc, eps, sigma, a, ginv, skin;
+};
+
+// LJ action (+ gradient) of one system: grid (tiles, chains).
+template <typename R>
+cudaError_t launch_lj_action(const R* pos, R* grad, double* partials, int slot0, int N, int T,
+                             int n_chains, long long sys_offset, const LJConst& c, int tile_steps,
+                             int tpp, int maxnb, bool with_grad, cudaStream_t st);
+
+// Shared memory the LJ kernel needs for (N, tpp, maxnb).
+size_t lj_smem_bytes(int N, int tpp, int maxnb, bool fp64);
+
+cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, int T, int n_chains,
+                                  long long sys_offset, double L, double rc, cudaStream_t st);
+
+// Euler-Maruyama reference paths.
+template <typename R>
+cudaError_t launch_ho_euler(R* pos, const R* noise, int s, int T, int n_chains, long long sys_offset,
+                            int chain0, double k, double a, double sig, uint64_t seed,
+                            uint64_t counter, cudaStream_t st);
+template <typename R>
+cudaError_t launch_lj_euler(R* pos, const R* noise, int N, int T, int n_chains, long long sys_offset,
+                            int chain0, const LJConst& c, int tpp, int maxnb, double sig,
+                            uint64_t seed, uint64_t counter, cudaStream_t st);
+
+// Deterministic per-chain sums of partials: out[c] = scale * sum(partials[slots[c]]).
+cudaError_t launch_finalize(const double* partials, const ChainSlots* slots, int n_chains,
+                            double scale, double* out, cudaStream_t st);
+
+// MALA update pieces (element-wise over all systems' blocks).
+struct MalaDev {
+    uint64_t seed;
+    uint64_t counter;
+    double h;
+};
+template <typename R>
+cudaError_t launch_mala_propose(const ElemBlock* blocks, int n_blocks, const R* pos, const R* grad,
+                                const R* noise, R* prop, double* part_qf, const MalaDev* md,
+                                int update_index, cudaStream_t st);
+template <typename R>
+cudaError_t launch_mala_reverse(const ElemBlock* blocks, int n_blocks, const R* pos, const R* prop,
+                                const R* grad_prop, double* part_qr, const MalaDev* md,
+                                cudaStream_t st);
+cudaError_t launch_mala_accept(int n_chains, const double* S, const double* S_prop,
+                               const double* qf, const double* qr, const double* log_u,
+                               const MalaDev* md, int update_index, int* accept_flag,
+                               int* n_accepted, double* log_alpha, cudaStream_t st);
+template <typename R>
+cudaError_t launch_mala_commit(const ElemBlock* blocks, int n_blocks, R* pos, R* grad, const R* prop,
+                               const R* grad_prop, const int* accept_flag, double* S,
+                               const double* S_prop, cudaStream_t st);
+cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter, double h,
+                                   cudaStream_t st);
+
+cudaError_t launch_philox(uint4 ctr, uint2 key, long long n, uint32_t* out, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain,
+                           long long e0, long long n, float* out, cudaStream_t st);
+
+}  // namespace pamd

@@ -1,0 +1,263 @@
+// update_kernels.cu -- deterministic per-chain reductions, the whole-path
+// Metropolis-adjusted Langevin update that consumes the path gradient, and
+// the random-number fill kernels.
+//
+// Update (tail slice x_0 fixed, Metropolis-Hastings acceptance as in the
+// paper's path sampling, Sec. III; the trial moves along -grad S):
+//   x'_t = x_t - h g_t + sqrt(2h) eta_t            (t >= 1),  x'_0 = x_0
+//   log alpha = S(x) - S(x') - q_rev/(4h) + q_fwd/(4h)
+//   q_fwd = sum_{t>=1} |x'_t - x_t + h g_t(x)|^2,  q_rev = sum_{t>=1} |x_t - x'_t + h g_t(x')|^2
+// accepted iff log u < log alpha.  Element-wise terms are formed in the data
+// precision from the stored values; every sum and the comparison are double.
+#include "pamd_internal.cuh"
+
+namespace pamd {
+
+// ------------------------------------------------------------------ finalize
+// One warp per chain: fixed lane assignment and a fixed shuffle tree, so the
+// result is bitwise reproducible.
+__global__ void finalize_kernel(const double* __restrict__ partials, const ChainSlots* __restrict__ slots,
+                                int n_chains, double scale, double* __restrict__ out)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_chains) return;
+    const ChainSlots cs = slots[warp];
+    double s = 0.0;
+    for (int q = cs.begin + lane; q < cs.end; q += 32) s += partials[q];
+    s = warp_sum(s);
+    if (lane == 0) out[warp] = s * scale;
+}
+
+cudaError_t launch_finalize(const double* partials, const ChainSlots* slots, int n_chains,
+                            double scale, double* out, cudaStream_t st)
+{
+    if (n_chains <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (n_chains * 32 + threads - 1) / threads;
+    finalize_kernel<<<blocks, threads, 0, st>>>(partials, slots, n_chains, scale, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ MALA pieces
+__global__ void set_mala_params_kernel(MalaDev* md, uint64_t seed, uint64_t counter, double h)
+{
+    md->seed = seed;
+    md->counter = counter;
+    md->h = h;
+}
+
+cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter, double h,
+                                   cudaStream_t st)
+{
+    set_mala_params_kernel<<<1, 1, 0, st>>>(md, seed, counter, h);
+    return cudaGetLastError();
+}
+
+// Each thread owns groups of 4 consecutive chain-local elements (one Philox
+// call gives the 4 normals of a group).
+template <typename R>
+__global__ void __launch_bounds__(kElemThreads)
+    mala_propose_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
+                        const R* __restrict__ grad, const R* __restrict__ noise, R* __restrict__ prop,
+                        double* __restrict__ part_qf, const MalaDev* __restrict__ md, int update_index)
+{
+    __shared__ double red[kElemThreads / 32];
+    const ElemBlock B = blocks[blockIdx.x];
+    const double hd = md->h;
+    const R h = (R)hd, s2h = (R)sqrt(2.0 * hd);
+    const uint64_t seed = md->seed, counter = md->counter + (uint64_t)update_index;
+    const long long base = B.chain_base;
+    R acc = R(0);
+    const int g0 = B.e0 >> 2;                 // e0 is a multiple of 4
+    const int ng = (B.n + 3) >> 2;
+    for (int gq = threadIdx.x; gq < ng; gq += kElemThreads) {
+        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!noise) z4 = philox_normals4(seed, counter, kStreamMala, (uint32_t)B.chain, (uint32_t)(g0 + gq));
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = B.e0 + 4 * gq + l;
+            if (e >= B.e0 + B.n) break;
+            const R x = pos[base + e];
+            if (e < B.s) {  // tail slice x_0 is held fixed
+                prop[base + e] = x;
+                continue;
+            }
+            const R g = grad[base + e];
+            const R z = noise ? noise[base + e] : (R)pick4(z4, l);
+            const R xp = x + fma_r(-h, g, s2h * z);
+            prop[base + e] = xp;
+            const R f = fma_r(h, g, xp - x);
+            acc = fma_r(f, f, acc);
+        }
+    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part_qf[blockIdx.x] = tot;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kElemThreads)
+    mala_reverse_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
+                        const R* __restrict__ prop, const R* __restrict__ grad_prop,
+                        double* __restrict__ part_qr, const MalaDev* __restrict__ md)
+{
+    __shared__ double red[kElemThreads / 32];
+    const ElemBlock B = blocks[blockIdx.x];
+    const R h = (R)md->h;
+    const long long base = B.chain_base;
+    R acc = R(0);
+#pragma unroll 4
+    for (int q = threadIdx.x; q < B.n; q += kElemThreads) {
+        const int e = B.e0 + q;
+        if (e < B.s) continue;
+        const R x = pos[base + e], xp = prop[base + e], gp = grad_prop[base + e];
+        const R b = fma_r(h, gp, x - xp);
+        acc = fma_r(b, b, acc);
+    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part_qr[blockIdx.x] = tot;
+}
+
+__global__ void mala_accept_kernel(int n_chains, const double* __restrict__ S,
+                                   const double* __restrict__ S_prop, const double* __restrict__ qf,
+                                   const double* __restrict__ qr, const double* __restrict__ log_u,
+                                   const MalaDev* __restrict__ md, int update_index,
+                                   int* __restrict__ accept_flag, int* __restrict__ n_accepted,
+                                   double* __restrict__ log_alpha)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    const double h4 = 4.0 * md->h;
+    const double la = (S[c] - S_prop[c]) - qr[c] / h4 + qf[c] / h4;
+    double lu;
+    if (log_u) {
+        lu = log_u[c];
+    } else {
+        lu = log(philox_uniform53(md->seed, md->counter + (uint64_t)update_index, kStreamAccept,
+                                  (uint32_t)c));
+    }
+    const int acc = (lu < la) ? 1 : 0;  // NaN log alpha never accepts
+    accept_flag[c] = acc;
+    if (n_accepted) n_accepted[c] += acc;
+    if (log_alpha) log_alpha[c] = la;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kElemThreads)
+    mala_commit_kernel(const ElemBlock* __restrict__ blocks, R* __restrict__ pos, R* __restrict__ grad,
+                       const R* __restrict__ prop, const R* __restrict__ grad_prop,
+                       const int* __restrict__ accept_flag, double* __restrict__ S,
+                       const double* __restrict__ S_prop)
+{
+    const ElemBlock B = blocks[blockIdx.x];
+    if (!accept_flag[B.chain]) return;
+    const long long base = B.chain_base;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < B.n; q += kElemThreads) {
+        const long long e = base + B.e0 + q;
+        pos[e] = prop[e];
+        grad[e] = grad_prop[e];
+    }
+    if (B.e0 == 0 && threadIdx.x == 0) S[B.chain] = S_prop[B.chain];
+}
+
+template <typename R>
+cudaError_t launch_mala_propose(const ElemBlock* blocks, int n_blocks, const R* pos, const R* grad,
+                                const R* noise, R* prop, double* part_qf, const MalaDev* md,
+                                int update_index, cudaStream_t st)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    mala_propose_kernel<R><<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, grad, noise, prop, part_qf,
+                                                              md, update_index);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_mala_reverse(const ElemBlock* blocks, int n_blocks, const R* pos, const R* prop,
+                                const R* grad_prop, double* part_qr, const MalaDev* md,
+                                cudaStream_t st)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    mala_reverse_kernel<R><<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, prop, grad_prop, part_qr, md);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mala_accept(int n_chains, const double* S, const double* S_prop,
+                               const double* qf, const double* qr, const double* log_u,
+                               const MalaDev* md, int update_index, int* accept_flag,
+                               int* n_accepted, double* log_alpha, cudaStream_t st)
+{
+    if (n_chains <= 0) return cudaSuccess;
+    const int threads = 128;
+    mala_accept_kernel<<<(n_chains + threads - 1) / threads, threads, 0, st>>>(
+        n_chains, S, S_prop, qf, qr, log_u, md, update_index, accept_flag, n_accepted, log_alpha);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_mala_commit(const ElemBlock* blocks, int n_blocks, R* pos, R* grad, const R* prop,
+                               const R* grad_prop, const int* accept_flag, double* S,
+                               const double* S_prop, cudaStream_t st)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    mala_commit_kernel<R><<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, grad, prop, grad_prop,
+                                                             accept_flag, S, S_prop);
+    return cudaGetLastError();
+}
+
+#define PAMD_INST(R)                                                                               \
+    template cudaError_t launch_mala_propose<R>(const ElemBlock*, int, const R*, const R*,         \
+                                                const R*, R*, double*, const MalaDev*, int,        \
+                                                cudaStream_t);                                     \
+    template cudaError_t launch_mala_reverse<R>(const ElemBlock*, int, const R*, const R*,         \
+                                                const R*, double*, const MalaDev*, cudaStream_t);  \
+    template cudaError_t launch_mala_commit<R>(const ElemBlock*, int, R*, R*, const R*, const R*,  \
+                                               const int*, double*, const double*, cudaStream_t);
+PAMD_INST(float)
+PAMD_INST(double)
+#undef PAMD_INST
+
+// ------------------------------------------------------------------ RNG fills
+__global__ void philox_fill_kernel(uint4 ctr, uint2 key, long long n, uint32_t* __restrict__ out)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint4 c = ctr;
+    const unsigned long long lo = (unsigned long long)c.x + (unsigned long long)q;
+    c.x = (uint32_t)lo;
+    const uint4 w = philox4x32_10(c, key);
+    out[4 * q + 0] = w.x;
+    out[4 * q + 1] = w.y;
+    out[4 * q + 2] = w.z;
+    out[4 * q + 3] = w.w;
+}
+
+cudaError_t launch_philox(uint4 ctr, uint2 key, long long n, uint32_t* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    philox_fill_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(ctr, key, n, out);
+    return cudaGetLastError();
+}
+
+__global__ void normals_fill_kernel(uint64_t seed, uint64_t counter, uint32_t stream_id,
+                                    uint32_t chain, long long e0, long long n, float* __restrict__ out)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const long long e = e0 + q;
+    const float4 z = philox_normals4(seed, counter, stream_id, chain, (uint32_t)(e >> 2));
+    out[q] = pick4(z, (int)(e & 3));
+}
+
+cudaError_t launch_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain,
+                           long long e0, long long n, float* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    normals_fill_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+        seed, counter, stream_id, chain, e0, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pamd

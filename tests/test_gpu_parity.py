@@ -1,0 +1,354 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: FP32 data with FP64 accumulation, 1e-5 relative on S and on the
+gradient (per chain, 2-norm) plus a max-abs bound of 1e-5 * max|g|; plain FP64,
+1e-12 relative.  Index work (pair counts, Philox words) is compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import pamd_inputs as inputs
+from _common import gpu_system, oracle_potential, rel, start_paths
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pamd():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1907_09529_gb300 as pamd
+    pamd.tune()  # automatic launch shapes
+    return pamd
+
+
+def _problem(pamd, w, precision, one=False):
+    return pamd.Problem([gpu_system(s, pamd) for s in w.systems], w.D, w.beta, w.dt,
+                        precision=precision, one_chain_per_launch=one)
+
+
+def _upload(pamd, prob, paths, device="cuda"):
+    buf = prob.empty(device)
+    for q, p in enumerate(paths):
+        prob.view(buf, q).copy_(torch.from_numpy(p).to(prob.dtype))
+    return buf
+
+
+def _check_against_oracle(w, prob, paths, S, g, tol_rel, nthreads=8):
+    S = S.cpu().numpy()
+    g = g.cpu()
+    worst = (0.0, 0.0)
+    for q, spec in enumerate(w.systems):
+        pot = oracle_potential(spec)
+        gq = prob.view(g, q).double().numpy()
+        for b in range(spec.n_chains):
+            So, go = oracle.action_grad(pot, paths[q][b], w.D, w.beta, w.dt, nthreads=nthreads)
+            c = prob.chain0[q] + b
+            es = abs(S[c] - So) / abs(So)
+            eg = rel(gq[b], go)
+            emax = np.abs(gq[b] - go).max() / np.abs(go).max()
+            assert es <= tol_rel, (q, b, es)
+            assert eg <= tol_rel, (q, b, eg)
+            assert emax <= tol_rel, (q, b, emax)
+            worst = (max(worst[0], es), max(worst[1], eg))
+    return worst
+
+
+@pytest.mark.parametrize("name", ["ho3d", "lj108", "lj500", "ragged"])
+def test_fp32_action_grad_matches_oracle(pamd, name):
+    w = inputs.workload(name, "small")
+    paths = start_paths(w, "fp32")
+    prob = _problem(pamd, w, "fp32")
+    buf = _upload(pamd, prob, paths)
+    S, g = pamd.action_grad(prob, buf)
+    torch.cuda.synchronize()
+    _check_against_oracle(w, prob, paths, S, g, 1e-5)
+    # action-only entry point gives the same S
+    S2 = pamd.action(prob, buf)
+    torch.cuda.synchronize()
+    assert torch.allclose(S2, S, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("name,one", [("ho1d", True), ("ho1d", False), ("lj108", True),
+                                      ("ragged", False)])
+def test_fp64_plain_matches_oracle(pamd, name, one):
+    w = inputs.workload(name, "small")
+    paths = start_paths(w, "fp64")
+    prob = _problem(pamd, w, "fp64", one=one)
+    buf = _upload(pamd, prob, paths)
+    S, g = pamd.action_grad(prob, buf)
+    torch.cuda.synchronize()
+    _check_against_oracle(w, prob, paths, S, g, 1e-12)
+
+
+def test_edge_cases_tiny_paths(pamd):
+    """T = 1 (two slices), N = 2 LJ particles, odd sizes and ragged tails."""
+    L = 6.0
+    systems = [pamd.System("lj", 2, 3, 1, 1, box=L, rc=2.5),
+               pamd.System("lj", 3, 3, 5, 2, box=L, rc=3.0),
+               pamd.System("harmonic", 1, 1, 1, 1, k=2.0),
+               pamd.System("harmonic", 5, 2, 4097, 2, k=0.5)]
+    prob = pamd.Problem(systems, 0.9, 1.1, 1e-3)
+    rng = inputs.rng(5)
+    paths = []
+    for s in systems:
+        base = rng.uniform(0, L, size=(s.n_chains, 1, s.d, s.N)) if s.kind == "lj" else 0
+        p = base + 0.05 * rng.standard_normal((s.n_chains, s.T + 1, s.d, s.N))
+        if s.kind == "lj":  # keep pairs apart
+            p[:, :, :, :] += np.arange(s.N)[None, None, None, :] * 1.3
+        paths.append(p.astype(np.float32).astype(np.float64))
+    buf = _upload(pamd, prob, paths)
+    S, g = pamd.action_grad(prob, buf)
+    torch.cuda.synchronize()
+    S, g = S.cpu().numpy(), g.cpu()
+    for q, s in enumerate(systems):
+        pot = (oracle.lennard_jones(s.box, s.rc) if s.kind == "lj" else oracle.harmonic(s.k))
+        for b in range(s.n_chains):
+            So, go = oracle.action_grad(pot, paths[q][b], 0.9, 1.1, 1e-3)
+            c = prob.chain0[q] + b
+            assert abs(S[c] - So) <= 1e-5 * abs(So)
+            assert rel(prob.view(g, q)[b].double().numpy(), go) <= 1e-5
+
+
+def test_results_independent_of_tiling(pamd):
+    """Candidate order is fixed, so the gradient is bitwise the same for any tile,
+    skin, list capacity (including the overflow path) and thread split."""
+    w = inputs.workload("lj108", "small")
+    paths = start_paths(w, "fp32")
+    outs = []
+    try:
+        for tile, tpp, maxnb, skin in [(32, 0, 0, -1), (1, 0, 0, -1), (7, 0, 0, 0.05),
+                                       (64, 0, 0, 0.6), (16, 0, 8, -1)]:
+            pamd.tune(tile, tpp, maxnb, skin)
+            prob = _problem(pamd, w, "fp32")
+            buf = _upload(pamd, prob, paths)
+            S, g = pamd.action_grad(prob, buf)
+            torch.cuda.synchronize()
+            outs.append((S.cpu(), g.cpu()))
+    finally:
+        pamd.tune()
+    for S, g in outs[1:]:
+        assert torch.equal(S, outs[0][0])
+        assert torch.equal(g, outs[0][1])
+
+
+def test_pair_counts_bit_exact(pamd):
+    w = inputs.workload("lj500", "small")
+    paths = start_paths(w, "fp32")
+    spec = w.systems[0]
+    prob = _problem(pamd, w, "fp32")
+    buf = _upload(pamd, prob, paths)
+    counts = pamd.lj_pair_counts(prob, buf).cpu().numpy()
+    T = spec.T
+    for b in range(spec.n_chains):
+        for t in range(0, T + 1, 7):
+            ref = oracle.pair_count_f32(spec.box, spec.rc_eff, paths[0][b, t].astype(np.float32))
+            assert counts[b * (T + 1) + t] == ref
+
+
+def test_philox_and_normals_match_oracle(pamd):
+    ctr, key = (0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0)
+    n = 1000
+    words = pamd.philox(ctr, key, n).cpu().numpy().view(np.uint32).reshape(n, 4)
+    for q in (0, 1, 517, n - 1):
+        c = list(ctr)
+        c[0] = (c[0] + q) & 0xFFFFFFFF
+        assert np.array_equal(words[q], oracle.philox(c, key))
+    z = pamd.normals(seed=1234567, counter=3, stream_id=1, chain=5, n=4099, e0=13).cpu().numpy()
+    zo = oracle.normals(1234567, 3, 1, 5, 4099, e0=13)
+    assert np.all(np.abs(z - zo) <= 2e-6 * (1 + np.abs(zo)))
+
+
+def test_euler_reference_matches_oracle(pamd):
+    # plain FP64 oscillator: exact recursion
+    w = inputs.workload("ho1d")
+    spec = w.systems[0]
+    prob = _problem(pamd, w, "fp64")
+    xi = inputs.euler_noise(spec, 77)
+    noise = np.zeros((1, spec.T + 1, 1, 1))
+    noise[:, 1:] = xi
+    buf = prob.empty("cuda")
+    nbuf = prob.empty("cuda")
+    prob.view(nbuf, 0).copy_(torch.from_numpy(noise))
+    pamd.euler_reference(prob, buf, noise=nbuf)
+    torch.cuda.synchronize()
+    ref = oracle.euler(oracle_potential(spec), np.zeros((1, 1)), xi[0], w.D, w.beta, w.dt)
+    got = prob.view(buf, 0)[0].cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * max(1, np.abs(ref).max())
+    # FP32 LJ, short path (chaos has no time to amplify roundoff)
+    w = inputs.workload("lj108", "small")
+    spec = w.systems[0]
+    T = 30
+    spec = inputs.SystemSpec("lj", spec.N, 3, T, 2)
+    prob = pamd.Problem([gpu_system(spec, pamd)], w.D, w.beta, w.dt)
+    x0 = inputs.initial_positions(spec, 1)
+    xi = inputs.euler_noise(spec, 78)
+    noise = np.zeros((2, T + 1, 3, spec.N))
+    noise[:, 1:] = xi
+    buf = prob.empty("cuda")
+    prob.view(buf, 0)[:, 0].copy_(torch.from_numpy(x0).float())
+    nbuf = prob.empty("cuda")
+    prob.view(nbuf, 0).copy_(torch.from_numpy(noise).float())
+    pamd.euler_reference(prob, buf, noise=nbuf)
+    torch.cuda.synchronize()
+    ref = oracle.euler_batch(oracle_potential(spec), x0, noise[:, 1:].astype(np.float32), w.D,
+                             w.beta, w.dt, store_f32=True)
+    got = prob.view(buf, 0).cpu().double().numpy()
+    assert np.max(np.abs(got - ref)) <= 2e-5
+    # Philox noise stream: the invariant S = sum xi^2 / 2 holds up to FP32 rounding
+    buf2 = prob.empty("cuda")
+    prob.view(buf2, 0)[:, 0].copy_(torch.from_numpy(x0).float())
+    pamd.euler_reference(prob, buf2, seed=99, counter=5)
+    S, _ = pamd.action_grad(prob, buf2)
+    zs = [pamd.normals(99, 5, 0, c, T * 3 * spec.N, e0=3 * spec.N).double().cpu()
+          for c in range(2)]
+    for c in range(2):
+        assert abs(S[c].item() - 0.5 * float((zs[c] ** 2).sum())) <= 1e-3 * S[c].item()
+
+
+def _mala_case(pamd, w, precision, h, seed):
+    paths = start_paths(w, precision)
+    prob = _problem(pamd, w, precision)
+    buf = _upload(pamd, prob, paths)
+    S, g = pamd.action_grad(prob, buf)
+    rng = inputs.rng(seed)
+    eta = [rng.standard_normal(p.shape) for p in paths]
+    if precision == "fp32":
+        eta = [e.astype(np.float32).astype(np.float64) for e in eta]
+    logu = np.log(rng.random(prob.n_chains))
+    nbuf = _upload(pamd, prob, eta)
+    lu = torch.from_numpy(logu).cuda()
+    nacc = torch.zeros(prob.n_chains, dtype=torch.int32, device="cuda")
+    la = torch.zeros(prob.n_chains, dtype=torch.float64, device="cuda")
+    S0, g0 = S.clone(), g.clone()
+    pamd.path_update(prob, buf, g, S, h, 1, noise=nbuf, log_u=lu, n_accepted=nacc, log_alpha=la)
+    torch.cuda.synchronize()
+    return prob, paths, eta, logu, S0.cpu().numpy(), g0.cpu(), buf.cpu(), g.cpu(), S.cpu().numpy(), \
+        nacc.cpu().numpy(), la.cpu().numpy()
+
+
+def test_mala_update_fp64_matches_oracle(pamd):
+    w = inputs.workload("ho1d")
+    prob, paths, eta, logu, S0, g0, pos1, g1, S1, nacc, la = _mala_case(pamd, w, "fp64", 2e-4, 3)
+    spec = w.systems[0]
+    pot = oracle_potential(spec)
+    go = prob.view(g0, 0)[0].numpy()
+    r = oracle.mala_step(pot, paths[0][0], S0[0], go, eta[0][0], logu[0], 2e-4, w.D, w.beta, w.dt)
+    assert abs(la[0] - r["log_alpha"]) <= 1e-9 * (1 + abs(r["log_alpha"]))
+    assert bool(nacc[0]) == r["accepted"]
+    expect = r["prop"] if r["accepted"] else paths[0][0]
+    assert np.max(np.abs(prob.view(pos1, 0)[0].numpy() - expect)) <= 1e-12
+    if r["accepted"]:
+        assert abs(S1[0] - r["S_prop"]) <= 1e-12 * r["S_prop"]
+
+
+def test_mala_update_fp32_matches_oracle(pamd):
+    w = inputs.workload("lj108", "small")
+    h = 2e-6
+    prob, paths, eta, logu, S0, g0, pos1, g1, S1, nacc, la = _mala_case(pamd, w, "fp32", h, 4)
+    spec = w.systems[0]
+    pot = oracle_potential(spec)
+    go = prob.view(g0, 0)[0].double().numpy()
+    r = oracle.mala_step(pot, paths[0][0], S0[0], go, eta[0][0], logu[0], h, w.D, w.beta, w.dt,
+                         store_f32=True, nthreads=8)
+    # log alpha agrees to the FP32 rounding of the proposal (a few 1e-3 absolute here)
+    assert abs(la[0] - r["log_alpha"]) <= 5e-3 * (1 + abs(r["log_alpha"]))
+    if abs(logu[0] - r["log_alpha"]) > 1e-2:
+        assert bool(nacc[0]) == r["accepted"]
+    expect = r["prop"] if nacc[0] else paths[0][0]
+    got = prob.view(pos1, 0)[0].double().numpy()
+    assert np.max(np.abs(got - expect)) <= 4 * np.spacing(np.float32(np.abs(expect).max()))
+
+
+def test_path_update_keeps_cached_action_consistent(pamd):
+    """After many updates (captured as a CUDA graph) the cached S and grad equal a
+    fresh evaluation of the updated path, and the tail slice never moved."""
+    w = inputs.workload("lj108", "small")
+    paths = start_paths(w, "fp32")
+    prob = _problem(pamd, w, "fp32")
+    buf = _upload(pamd, prob, paths)
+    S, g = pamd.action_grad(prob, buf)
+    nacc = torch.zeros(prob.n_chains, dtype=torch.int32, device="cuda")
+    x0 = prob.view(buf, 0)[:, 0].clone()
+    pamd.path_update(prob, buf, g, S, 1e-6, n_updates=20, seed=11, counter=100, n_accepted=nacc)
+    pamd.path_update(prob, buf, g, S, 1e-6, n_updates=20, seed=11, counter=120, n_accepted=nacc)
+    torch.cuda.synchronize()
+    S2, g2 = pamd.action_grad(prob, buf)
+    torch.cuda.synchronize()
+    assert torch.equal(S2, S)
+    assert torch.equal(g2, g)
+    assert torch.equal(prob.view(buf, 0)[:, 0], x0)
+    assert 0 < int(nacc.sum()) <= 40 * prob.n_chains
+
+
+def test_host_buffers_match_device_buffers(pamd):
+    w = inputs.workload("ragged", "small")
+    paths = start_paths(w, "fp32")
+    prob = _problem(pamd, w, "fp32")
+    dbuf = _upload(pamd, prob, paths)
+    hbuf = dbuf.cpu().pin_memory()
+    Sd, gd = pamd.action_grad(prob, dbuf)
+    torch.cuda.synchronize()
+    Sh = torch.zeros(prob.n_chains, dtype=torch.float64).pin_memory()
+    gh = torch.zeros_like(hbuf).pin_memory()
+    pamd.action_grad(prob, hbuf, Sh, gh)
+    assert torch.equal(Sh, Sd.cpu())
+    assert torch.equal(gh, gd.cpu())
+    # pageable host memory works too
+    hp = dbuf.cpu()
+    Sp, gp = pamd.action_grad(prob, hp)
+    assert torch.equal(Sp, Sd.cpu()) and torch.equal(gp, gd.cpu())
+
+
+def test_autograd_function_and_finite_differences(pamd):
+    """PamdAction: backward is the hand-written adjoint; it matches central finite
+    differences of the kernel's own action (h = 1e-3, FP64 path) and the oracle."""
+    w = inputs.workload("lj108", "small")
+    spec = inputs.SystemSpec("lj", 108, 3, 24, 1)
+    w = inputs.Workload("lj108", [spec], dt=1e-4)
+    paths = start_paths(w, "fp64")
+    prob = _problem(pamd, w, "fp64")
+    buf = _upload(pamd, prob, paths).requires_grad_(True)
+    S = pamd.PamdAction.apply(buf, prob)
+    S.sum().backward()
+    g = buf.grad.detach()
+    rng = inputs.rng(17)
+    for _ in range(4):
+        v = torch.from_numpy(rng.standard_normal(prob.span)).cuda()
+        v /= v.norm()
+        hh = 1e-3
+        Sp = pamd.action(prob, (buf.detach() + hh * v).contiguous())
+        Sm = pamd.action(prob, (buf.detach() - hh * v).contiguous())
+        fd = float((Sp - Sm).sum()) / (2 * hh)
+        an = float((g * v).sum())
+        assert abs(fd - an) <= 1e-4 * (abs(an) + 1e-3 * float(g.norm()))
+    So, go = oracle.action_grad(oracle_potential(spec), paths[0][0], w.D, w.beta, w.dt)
+    assert rel(prob.view(g.cpu(), 0)[0].numpy(), go) <= 1e-12
+    # fp32 through autograd, weighted backward
+    prob32 = _problem(pamd, w, "fp32")
+    b32 = _upload(pamd, prob32, [p.astype(np.float32).astype(np.float64) for p in paths])
+    b32.requires_grad_(True)
+    S32 = pamd.PamdAction.apply(b32, prob32)
+    (3.0 * S32).sum().backward()
+    _, g32 = pamd.action_grad(prob32, b32.detach())
+    assert torch.allclose(b32.grad, 3.0 * g32, rtol=1e-6, atol=0)
+
+
+def test_invalid_arguments_are_rejected(pamd):
+    with pytest.raises(pamd.PamdError):
+        prob = pamd.Problem([pamd.System("lj", 10, 3, 4, 1, box=4.0, rc=2.5)], 1, 1, 1e-4)
+        pamd.action(prob, prob.empty("cuda"))  # rc > box/2
+    with pytest.raises(pamd.PamdError):
+        prob = pamd.Problem([pamd.System("lj", 2000, 3, 4, 1, box=40.0, rc=2.5)], 1, 1, 1e-4)
+        pamd.action(prob, prob.empty("cuda"))  # N beyond the supported maximum
+    prob = pamd.Problem([pamd.System("harmonic", 1, 1, 8, 1)], 1, 1, 1e-2)
+    buf = prob.empty("cuda")
+    S = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(pamd.PamdError):
+        pamd.path_update(prob, buf, buf.clone(), S, h=-1.0)
