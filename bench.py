@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--T", type=int, default=0, help="override steps per chain (profiling)")
+    ap.add_argument("--chains", type=int, default=0, help="override chains per system (profiling)")
+    ap.add_argument("--only-kernel", action="store_true",
+                    help="time only the action+gradient call (small profiling runs)")
     return ap.parse_args()
 
 
@@ -219,8 +223,12 @@ def launches_per_update(prob):
 
 def main():
     args = parse()
+    import dataclasses
     import pamd_inputs as inputs
     w = inputs.workload(args.config)
+    if args.T or args.chains:
+        w = dataclasses.replace(w, systems=[dataclasses.replace(
+            s, T=args.T or s.T, n_chains=args.chains or s.n_chains) for s in w.systems])
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -272,6 +280,23 @@ def main():
 
     def step(i):
         pamd.path_update(prob, pos, grad, S, h, 1, seed=seed, counter=1000 + i, n_accepted=nacc)
+
+    if args.only_kernel:
+        for _ in range(args.warmup):
+            pamd.action_grad(prob, pos, S, grad)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pamd.action_grad(prob, pos, S, grad)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rank == 0:
+            ms = e0.elapsed_time(e1) / max(1, args.steps)
+            print(json.dumps({"only_kernel": True, "workload": workload_desc(w), "ms_per_call": ms,
+                              "units_per_call": units_rank,
+                              "units_per_s": units_rank / (ms * 1e-3)}), flush=True)
+        return
 
     for i in range(args.warmup):
         step(i)

@@ -158,9 +158,9 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
 
 /* Diagnostics for bit-exact index parity: number of ordered in-cutoff pairs
  * (i != j) of every slice of every LJ chain, decided in single precision by
- * the kernels' rule (dx = xi - xj; dx = fmaf(-L, rintf(dx * (1/L)), dx);
- * r2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx)); in iff r2 <= rc*rc), with
- * L, 1/L, rc*rc rounded to float.  PAMD_FP32 problems only.
+ * the kernels' rule (dx = xi - xj; k = fmaf(dx, 1/L, 1.5*2^23) - 1.5*2^23;
+ * dx = fmaf(-L, k, dx); r2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx)); in iff
+ * r2 <= rc*rc), with L, 1/L, rc*rc rounded to float.  PAMD_FP32 only.
  *   counts : long long[sum over LJ chains of (T+1)], chain-major, written. */
 int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* counts,
                         void* stream);

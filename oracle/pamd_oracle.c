@@ -492,7 +492,8 @@ double or_uniform(uint64_t seed, uint64_t counter, uint32_t stream, uint32_t cha
  * shared with the GPU (an integer decided by floating point is compared
  * bit for bit, so both sides decide in the kernel's precision):
  *   Lf = (float)box, iLf = 1.0f / Lf, rc2f = (float)rc * (float)rc,
- *   dx = xi - xj;  dx = fmaf(-Lf, rintf(dx * iLf), dx)   (per component)
+ *   dx = xi - xj;  k = fmaf(dx, iLf, 1.5*2^23) - 1.5*2^23  (nearest integer
+ *   to the exact product);  dx = fmaf(-Lf, k, dx)            (per component)
  *   r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));   include iff r2 <= rc2f.
  * x is one slice [3][N] in single precision. */
 long long or_pair_count_f32(int N, double box, double rc, const float* x)
@@ -508,7 +509,7 @@ long long or_pair_count_f32(int N, double box, double rc, const float* x)
             float dxyz[3];
             for (int c = 0; c < 3; ++c) {
                 float dx = x[c * N + i] - x[c * N + j];
-                float sh = rintf(dx * iLf);
+                float sh = fmaf(dx, iLf, 12582912.0f) - 12582912.0f;
                 dxyz[c] = fmaf(-Lf, sh, dx);
             }
             float xx = dxyz[0] * dxyz[0];

@@ -136,7 +136,7 @@ def action_grad(p: Problem, pos: torch.Tensor, S: Optional[torch.Tensor] = None,
     if S is None:
         S = torch.empty(p.n_chains, dtype=torch.float64, device=pos.device)
     if grad is None:
-        grad = torch.empty_like(pos)
+        grad = torch.zeros_like(pos)  # padding between systems stays defined
     pamd_action_grad(p.ref, _ptr(pos), _ptr(S), _ptr(grad), _stream(pos, stream))
     return S, grad
 

@@ -32,7 +32,7 @@ namespace pamd {
 template <typename R>
 struct LJK {
     R L, iL, rc2, rl2, hs2;  // box, 1/box, rc^2, list radius^2, (skin/2)^2
-    R e24, sig6, duc;        // 24 eps, sigma^6, u'(rc)
+    R c1, c2, c3, duc;       // 24 eps sigma^6, 2 sigma^6, 26 sigma^6, u'(rc)
     R a, ginv, sig_em;       // beta D dt, 1/(2 D dt), sqrt(2 D dt)
 };
 
@@ -60,8 +60,9 @@ static LJK<R> make_lj_consts(const LJConst& c, double sig_em)
     }
     k.rl2 = (R)(rl * rl);
     k.hs2 = (R)(0.25 * c.skin * c.skin);
-    k.e24 = (R)(24.0 * c.eps);
-    k.sig6 = (R)s6;
+    k.c1 = (R)(24.0 * c.eps * s6);
+    k.c2 = (R)(2.0 * s6);
+    k.c3 = (R)(26.0 * s6);
     k.duc = (R)duc;
     k.a = (R)c.a;
     k.ginv = (R)c.ginv;
@@ -69,7 +70,19 @@ static LJK<R> make_lj_consts(const LJConst& c, double sig_em)
     return k;
 }
 
-// Minimum-image pair vector and |r_ij|^2 by the documented rule.
+// Round-to-nearest-even of the exact product a*b (|a*b| < 2^22), by adding and
+// removing 1.5*2^23 (float) or 1.5*2^52 (double): one FMA and one add.
+__device__ __forceinline__ float round_prod(float a, float b)
+{
+    return __fsub_rn(__fmaf_rn(a, b, 12582912.0f), 12582912.0f);
+}
+__device__ __forceinline__ double round_prod(double a, double b)
+{
+    return __dsub_rn(__fma_rn(a, b, 6755399441055744.0), 6755399441055744.0);
+}
+
+// Minimum-image pair vector and |r_ij|^2 by the documented rule:
+//   dx = xi - xj;  dx = fma(-L, round(dx * (1/L)), dx);  r2 = fma(dz,dz,fma(dy,dy,dx*dx)).
 template <typename R>
 __device__ __forceinline__ R pair_r2(R xi, R yi, R zi, const vec4_t<R>& pj, const LJK<R>& k, R& dx,
                                      R& dy, R& dz)
@@ -77,19 +90,34 @@ __device__ __forceinline__ R pair_r2(R xi, R yi, R zi, const vec4_t<R>& pj, cons
     dx = xi - pj.x;
     dy = yi - pj.y;
     dz = zi - pj.z;
-    dx = fma_r(-k.L, rint_r(mul_r(dx, k.iL)), dx);
-    dy = fma_r(-k.L, rint_r(mul_r(dy, k.iL)), dy);
-    dz = fma_r(-k.L, rint_r(mul_r(dz, k.iL)), dz);
+    dx = fma_r(-k.L, round_prod(dx, k.iL), dx);
+    dy = fma_r(-k.L, round_prod(dy, k.iL), dy);
+    dz = fma_r(-k.L, round_prod(dz, k.iL), dz);
     return fma_r(dz, dz, fma_r(dy, dy, mul_r(dx, dx)));
 }
 
-// -U'(r)/r for r^2 <= rc^2 (ri = 1/r, ir2 = 1/r^2).
-template <typename R>
-__device__ __forceinline__ R force_scalar(R ri, R ir2, const LJK<R>& k, R& s6_out)
+// Reciprocal square root: the hardware approximation in single precision
+// (relative error below 2^-22), the library function in double.
+__device__ __forceinline__ float rsqrt_fast(float v)
 {
-    const R s6 = k.sig6 * ir2 * ir2 * ir2;
-    s6_out = s6;
-    return fma_r(k.e24 * ir2 * s6, R(2) * s6 - R(1), k.duc * ri);
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double rsqrt_fast(double v) { return rsqrt(v); }
+
+// Pair scalars from r^2 (inside the cutoff):
+//   fs  = -U'(r)/r = ir2 * u * t + u'(rc)/r,  u = c1 ir6, t = c2 ir6 - 1
+//   upp = U''(r)   = ir2 * u * (c3 ir6 - 7)
+template <typename R>
+__device__ __forceinline__ R pair_fs(R r2, const LJK<R>& k, R& ir2, R& u, R& ir6)
+{
+    const R ri = rsqrt_fast(r2);
+    ir2 = ri * ri;
+    ir6 = ir2 * ir2 * ir2;
+    u = k.c1 * ir6;
+    const R t = fma_r(k.c2, ir6, R(-1));
+    return fma_r(u * t, ir2, k.duc * ri);
 }
 
 template <typename R, int TPP>
@@ -155,7 +183,9 @@ struct LJBlock {
         }
     }
 
-    // F(x) of particle i (complete in every thread of the group).
+    // F(x) of particle i (complete in every thread of the group).  Single
+    // precision is branch-free (every list entry evaluated, masked by the cutoff
+    // test); double precision skips the costly math outside the cutoff.
     __device__ void force(const V4* __restrict__ buf, const LJK<R>& k, R& fx, R& fy, R& fz) const
     {
         fx = fy = fz = R(0);
@@ -164,15 +194,13 @@ struct LJBlock {
             for_each_candidate([&](int j) {
                 R dx, dy, dz;
                 const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
-                if (r2 <= k.rc2) {
-                    const R ri = rsqrt_r(r2);
-                    const R ir2 = ri * ri;
-                    R s6;
-                    const R fs = force_scalar<R>(ri, ir2, k, s6);
-                    fx = fma_r(fs, dx, fx);
-                    fy = fma_r(fs, dy, fy);
-                    fz = fma_r(fs, dz, fz);
-                }
+                if (sizeof(R) == 8 && !(r2 <= k.rc2)) return;
+                R ir2, u, ir6;
+                R fs = pair_fs<R>(r2, k, ir2, u, ir6);
+                fs = (r2 <= k.rc2) ? fs : R(0);
+                fx = fma_r(fs, dx, fx);
+                fy = fma_r(fs, dy, fy);
+                fz = fma_r(fs, dz, fz);
             });
         }
         group_sum(fx, fy, fz);
@@ -188,21 +216,19 @@ struct LJBlock {
             for_each_candidate([&](int j) {
                 R dx, dy, dz;
                 const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
-                if (r2 <= k.rc2) {
-                    const R ri = rsqrt_r(r2);
-                    const R ir2 = ri * ri;
-                    R s6;
-                    const R A = -force_scalar<R>(ri, ir2, k, s6);     // U'(r)/r
-                    const R upp = k.e24 * ir2 * s6 * fma_r(R(26), s6, R(-7));  // U''(r)
-                    const R Bc = (upp - A) * ir2;
-                    const V4 vj = vbuf[j];
-                    const R vx = vix - vj.x, vy = viy - vj.y, vz = viz - vj.z;
-                    const R dot = fma_r(dz, vz, fma_r(dy, vy, dx * vx));
-                    const R bd = Bc * dot;
-                    hx = fma_r(A, vx, fma_r(bd, dx, hx));
-                    hy = fma_r(A, vy, fma_r(bd, dy, hy));
-                    hz = fma_r(A, vz, fma_r(bd, dz, hz));
-                }
+                if (sizeof(R) == 8 && !(r2 <= k.rc2)) return;
+                R ir2, u, ir6;
+                const R fs = pair_fs<R>(r2, k, ir2, u, ir6);      // -U'(r)/r
+                const R upp = ir2 * u * fma_r(k.c3, ir6, R(-7));  // U''(r)
+                const bool in = r2 <= k.rc2;
+                const R mA = in ? fs : R(0);                      // -(U'/r), masked
+                const R Bc = in ? (upp + fs) * ir2 : R(0);        // (U'' - U'/r)/r^2, masked
+                const V4 vj = vbuf[j];
+                const R vx = vix - vj.x, vy = viy - vj.y, vz = viz - vj.z;
+                const R bd = Bc * fma_r(dz, vz, fma_r(dy, vy, dx * vx));
+                hx = fma_r(-mA, vx, fma_r(bd, dx, hx));
+                hy = fma_r(-mA, vy, fma_r(bd, dy, hy));
+                hz = fma_r(-mA, vz, fma_r(bd, dz, hz));
             });
         }
         group_sum(hx, hy, hz);
@@ -227,8 +253,8 @@ struct LJArgs {
     LJK<R> k;
 };
 
-template <typename R, int TPP, bool GRAD>
-__global__ void __launch_bounds__(1024) lj_action_kernel(const LJArgs<R> A)
+template <typename R, int TPP, bool GRAD, int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1)) lj_action_kernel(const LJArgs<R> A)
 {
     using V4 = vec4_t<R>;
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -353,10 +379,10 @@ template <typename R, int TPP, bool GRAD>
 static cudaError_t launch_lj_t(const LJArgs<R>& A, int n_tiles, int n_chains, size_t smem,
                                cudaStream_t st)
 {
-    auto kern = lj_action_kernel<R, TPP, GRAD>;
+    const int NT = ((A.N * TPP + 31) / 32) * 32;
+    auto kern = NT <= 512 ? lj_action_kernel<R, TPP, GRAD, 512> : lj_action_kernel<R, TPP, GRAD, 1024>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int NT = ((A.N * TPP + 31) / 32) * 32;
     kern<<<dim3(n_tiles, n_chains), NT, smem, st>>>(A);
     return cudaGetLastError();
 }

@@ -158,23 +158,29 @@ int max_dynamic_smem()
     return v;
 }
 
-// Default LJ launch shape: threads per particle, Verlet skin, list capacity, tile.
+// Default LJ launch shape: threads per particle (N * tpp <= 512 where possible,
+// so that two CTAs share an SM), Verlet skin, list capacity, tile length.
 LJTune choose_lj_tune(const pamd_system& s, bool fp64)
 {
     LJTune t;
     const int N = s.n_particles;
-    t.tpp = g_tune_override.tpp > 0 ? g_tune_override.tpp : (N <= 256 ? 4 : (N <= 512 ? 2 : 1));
+    if (fp64)  // double precision: more threads per particle (latency of FP64 math)
+        t.tpp = g_tune_override.tpp > 0 ? g_tune_override.tpp : (N <= 256 ? 4 : (N <= 512 ? 2 : 1));
+    else
+        t.tpp = g_tune_override.tpp > 0 ? g_tune_override.tpp : (N <= 128 ? 4 : (N <= 256 ? 2 : 1));
     while (t.tpp > 1 && N * t.tpp > 1024) t.tpp >>= 1;
     t.skin = g_tune_override.skin >= 0 ? g_tune_override.skin : 0.25;
     t.tile_steps = g_tune_override.tile_steps > 0 ? g_tune_override.tile_steps : 32;
     const double L = s.pot.box, rho = N / (L * L * L), rl = s.pot.rc + t.skin;
     const double expect = 4.18879020478639 * rl * rl * rl * rho;  // 4/3 pi rl^3 rho
-    int want = (int)(1.3 * expect) + 16;
+    int want = (int)(1.2 * expect) + 8;
     if (want > N - 1 + t.tpp) want = N - 1 + t.tpp;
     if (g_tune_override.maxnb > 0) want = g_tune_override.maxnb;
     want = ((want + t.tpp - 1) / t.tpp) * t.tpp;
-    // shrink until it fits in shared memory
-    const int smax = max_dynamic_smem() - 1024;
+    // shrink until it fits: two CTAs per SM for blocks of <= 512 threads
+    const int NT = ((N * t.tpp + 31) / 32) * 32;
+    const int smax = (NT <= 512 && !fp64 && g_tune_override.maxnb <= 0) ? 113 * 1024
+                                                                        : max_dynamic_smem() - 1024;
     while (want > t.tpp && (int)lj_smem_bytes(N, t.tpp, want, fp64) > smax) want -= t.tpp;
     t.maxnb = want;
     return t;
