@@ -189,6 +189,36 @@ int pamd_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t c
  * against concurrent calls. */
 int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin);
 
+/* Harmonic action and gradient that allocates nothing (no counterpart in the
+ * paper; it exists for callers, not for the method).
+ *
+ * Some callers cannot allocate device memory once they are running: a
+ * process whose allocator has already reserved the GPU's memory for itself,
+ * or a service that forbids cudaMalloc/cudaFree after start-up because they
+ * synchronise the device and can fail under memory pressure.  This entry
+ * point computes exactly what pamd_action_grad computes for harmonic systems,
+ * using only the caller's buffers plus a fixed scratch array compiled into
+ * the library: PAMD_NOALLOC_MAX_BLOCKS doubles (512 KiB) of block sums, one
+ * per 4096 elements of every chain.  Every GPU that loads the library holds
+ * that array until the process exits.
+ *   prob : harmonic systems only (PAMD_FP32 or PAMD_FP64); otherwise
+ *          PAMD_ERR_ARG.  A problem needing more than PAMD_NOALLOC_MAX_BLOCKS
+ *          blocks (sum over chains of ceil((T+1)*dim*N / 4096)) is rejected
+ *          with PAMD_ERR_UNSUPPORTED before anything runs.
+ *   pos, S, grad : device pointers (host pointers: PAMD_ERR_ARG), as in
+ *          pamd_action_grad.
+ * No cudaMalloc, cudaFree or allocating library call is made.  The first call
+ * on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (every block sum is written before it is read, so
+ * nothing needs clearing); calls whose kernels overlap on the GPU -- on two
+ * streams, or from two threads -- race on it and must be serialised by the
+ * caller. */
+#define PAMD_NOALLOC_MAX_BLOCKS 65536
+int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void* pos, double* S, void* grad,
+                                void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* pamd_status_string(int status);
 

@@ -31,8 +31,11 @@ PAMD_FLAG_ONE_CHAIN_PER_LAUNCH = 1
 EXPORTS = (
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
-    "pamd_release_cache", "pamd_version", "pamd_tune",
+    "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
 )
+
+#: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
+PAMD_NOALLOC_MAX_BLOCKS = 65536
 
 
 class pamd_potential(ctypes.Structure):
@@ -91,6 +94,7 @@ def load(path: str = LIB_PATH):
             "pamd_version": (ctypes.c_int, []),
             "pamd_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double]),
+            "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -153,3 +157,9 @@ def pamd_release_cache():
 
 def pamd_version():
     return load().pamd_version()
+
+
+def pamd_ho_action_grad_noalloc(prob, pos, S, grad, stream):
+    """Harmonic action + gradient using only the caller's buffers and the
+    library's fixed scratch array (no device allocation); see include/pamd.h."""
+    return _call("pamd_ho_action_grad_noalloc", prob, pos, S, grad, stream)
