@@ -12,11 +12,13 @@
 //   r_t = x_{t+1} - x_t - a F(x_t)                          (Eq. (3))
 //   g_t = [r_{t-1} - r_t + a H(x_t) r_t] / (2 D dt),  r_{-1} = r_T = 0.
 //
-// Work decomposition.  One CTA per (chain, tile of TS consecutive steps).  The
+// Work decomposition.  A persistent grid pulls work items -- (system, chain,
+// tile of consecutive steps) -- from an atomic queue, largest first, so that
+// chains and systems of different N and T share one launch.  For an item the
 // current slice x_t and the next x_{t+1} live in shared memory as 4-vectors, as
 // does r_t (the Hessian-vector product needs the residuals of the neighbours).
-// Each particle owns TPP adjacent threads; thread q of particle i handles the
-// candidates j = q (mod TPP).  A Verlet list of radius rc + skin, built from the
+// Each particle owns TPP adjacent threads (TPP per system, a power of two);
+// thread q of particle i handles the candidates j = q (mod TPP).  A Verlet list of radius rc + skin, built from the
 // slice at the tile start, is kept in shared memory and reused for the following
 // slices: it stays exact while no particle has moved more than skin/2 from the
 // position it had when the list was built (then no pair can have crossed from
@@ -28,47 +30,6 @@
 #include "pamd_internal.cuh"
 
 namespace pamd {
-
-template <typename R>
-struct LJK {
-    R L, iL, rc2, rl2, hs2;  // box, 1/box, rc^2, list radius^2, (skin/2)^2
-    R c1, c2, c3, duc;       // 24 eps sigma^6, 2 sigma^6, 26 sigma^6, u'(rc)
-    R a, ginv, sig_em;       // beta D dt, 1/(2 D dt), sqrt(2 D dt)
-};
-
-template <typename R>
-static LJK<R> make_lj_consts(const LJConst& c, double sig_em)
-{
-    LJK<R> k;
-    const double rl = c.rc + c.skin;
-    const double s6 = c.sigma * c.sigma * c.sigma * c.sigma * c.sigma * c.sigma;
-    const double src = c.sigma / c.rc;
-    const double q6 = src * src * src * src * src * src;
-    // u'(rc) = 4 eps (-12 (s/rc)^12 + 6 (s/rc)^6) / rc
-    const double duc = 4.0 * c.eps * (-12.0 * q6 * q6 + 6.0 * q6) / c.rc;
-    if (sizeof(R) == sizeof(float)) {
-        // The single-precision cutoff rule: L, 1/L and rc^2 rounded to float.
-        const float Lf = (float)c.L;
-        const float rcf = (float)c.rc;
-        k.L = (R)Lf;
-        k.iL = (R)(1.0f / Lf);
-        k.rc2 = (R)(rcf * rcf);
-    } else {
-        k.L = (R)c.L;
-        k.iL = (R)(1.0 / c.L);
-        k.rc2 = (R)(c.rc * c.rc);
-    }
-    k.rl2 = (R)(rl * rl);
-    k.hs2 = (R)(0.25 * c.skin * c.skin);
-    k.c1 = (R)(24.0 * c.eps * s6);
-    k.c2 = (R)(2.0 * s6);
-    k.c3 = (R)(26.0 * s6);
-    k.duc = (R)duc;
-    k.a = (R)c.a;
-    k.ginv = (R)c.ginv;
-    k.sig_em = (R)sig_em;
-    return k;
-}
 
 // Round-to-nearest-even of the exact product a*b (|a*b| < 2^22), by adding and
 // removing 1.5*2^23 (float) or 1.5*2^52 (double): one FMA and one add.
@@ -120,15 +81,31 @@ __device__ __forceinline__ R pair_fs(R r2, const LJK<R>& k, R& ir2, R& u, R& ir6
     return fma_r(u * t, ir2, k.duc * ri);
 }
 
-template <typename R, int TPP>
+
+template <typename R>
 struct LJBlock {
     using V4 = vec4_t<R>;
-    int N, NT, tid, i, q, cap;
+    int N, NT, tid, i, q, tpp, cap;
     bool active;
     uint16_t* nbr;  // nbr[m * NT + tid], m < cap
     int cnt;
     bool ovf;
     R xr, yr, zr;   // position at the last list build
+
+    __device__ void init(int n, int tpp_, int lg, int cap_, uint16_t* list)
+    {
+        N = n;
+        NT = blockDim.x;
+        tid = threadIdx.x;
+        tpp = tpp_;
+        i = tid >> lg;
+        q = tid & (tpp_ - 1);
+        active = i < n;
+        cap = cap_;
+        nbr = list;
+        cnt = 0;
+        ovf = false;
+    }
 
     __device__ void build(const V4* __restrict__ buf, const LJK<R>& k)
     {
@@ -140,7 +117,7 @@ struct LJBlock {
         yr = p.y;
         zr = p.z;
         int c = 0;
-        for (int j = q; j < N; j += TPP) {
+        for (int j = q; j < N; j += tpp) {
             if (j == i) continue;
             R dx, dy, dz;
             const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
@@ -161,6 +138,17 @@ struct LJBlock {
         return dx * dx + dy * dy + dz * dz > k.hs2;
     }
 
+    __device__ __forceinline__ void group_sum(R& x, R& y, R& z) const
+    {
+        for (int o = tpp >> 1; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+    }
+
+    // Candidates of particle i handled by this thread, in increasing j: the
+    // Verlet list, or every other particle when the list overflowed.
     template <typename F>
     __device__ __forceinline__ void for_each_candidate(F&& f) const
     {
@@ -168,18 +156,8 @@ struct LJBlock {
         if (!ovf) {
             for (int m = 0; m < cnt; ++m) f((int)nbr[m * NT + tid]);
         } else {
-            for (int j = q; j < N; j += TPP)
+            for (int j = q; j < N; j += tpp)
                 if (j != i) f(j);
-        }
-    }
-
-    __device__ __forceinline__ void group_sum(R& x, R& y, R& z) const
-    {
-#pragma unroll
-        for (int o = TPP / 2; o > 0; o >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, o);
-            y += __shfl_xor_sync(0xffffffffu, y, o);
-            z += __shfl_xor_sync(0xffffffffu, z, o);
         }
     }
 
@@ -242,53 +220,33 @@ __device__ __forceinline__ void load_slice(vec4_t<R>* buf, const R* __restrict__
         buf[n] = make4<R>(__ldg(Xt + n), __ldg(Xt + N + n), __ldg(Xt + 2 * N + n));
 }
 
-template <typename R>
-struct LJArgs {
-    const R* pos;
-    R* grad;
-    double* partials;
-    int slot0;
-    int N, T, TS, cap;
-    long long sys_offset;
-    LJK<R> k;
-};
-
-template <typename R, int TPP, bool GRAD, int MAXT>
-__global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1)) lj_action_kernel(const LJArgs<R> A)
+// One work item: steps [t0, t1) of one chain.  Writes g_t for t0 <= t < t1 (and
+// g_T when t1 == T) and the item's sum of |r_t|^2 into partials[slot].
+template <typename R, bool GRAD>
+__device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, unsigned char* smem,
+                                        int nmax, const R* __restrict__ pos, R* __restrict__ grad,
+                                        double* __restrict__ partials, double* red)
 {
     using V4 = vec4_t<R>;
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    __shared__ double red[32];
-    const int N = A.N;
-    V4* xa = reinterpret_cast<V4*>(smem_raw);
-    V4* xb = xa + N;
-    V4* rv = xb + N;
+    const int N = S.N;
+    V4* xa = reinterpret_cast<V4*>(smem);
+    V4* xb = xa + nmax;
+    V4* rv = xb + nmax;
+    LJBlock<R> L;
+    L.init(N, S.tpp, S.lg_tpp, S.cap, reinterpret_cast<uint16_t*>(rv + nmax));
+    const LJK<R>& k = S.k;
 
-    LJBlock<R, TPP> L;
-    L.N = N;
-    L.NT = blockDim.x;
-    L.tid = threadIdx.x;
-    L.i = threadIdx.x / TPP;
-    L.q = threadIdx.x % TPP;
-    L.active = L.i < N;
-    L.cap = A.cap;
-    L.nbr = reinterpret_cast<uint16_t*>(rv + N);
-    const LJK<R>& k = A.k;
-
-    const int chain = blockIdx.y, tile = blockIdx.x;
-    const int t0 = tile * A.TS;
-    const int t1 = min(A.T, t0 + A.TS);
+    const int t0 = I.t0, t1 = I.t1, T = S.T;
     const int s = 3 * N;
-    const long long chain_len = (long long)(A.T + 1) * s;
-    const R* __restrict__ X = A.pos + A.sys_offset + chain * chain_len;
-    R* __restrict__ G = GRAD ? A.grad + A.sys_offset + chain * chain_len : nullptr;
+    const R* __restrict__ X = pos + S.off + (long long)I.chain * S.chain_len;
+    R* __restrict__ G = GRAD ? grad + S.off + (long long)I.chain * S.chain_len : nullptr;
     const int i = L.i;
     const bool lead = L.active && L.q == 0;
 
     R rpx = R(0), rpy = R(0), rpz = R(0);  // r_{t-1}
     double acc = 0.0;
 
-    // Prologue: list at the first slice the tile touches; r_{t0-1} if t0 > 0.
+    // Prologue: list at the first slice the item touches; r_{t0-1} if t0 > 0.
     const int tf = t0 > 0 ? t0 - 1 : t0;
     load_slice<R>(xa, X + (long long)tf * s, N);
     __syncthreads();
@@ -357,98 +315,105 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1)) lj_action_kernel(
         xb = tmp;
         if (pf) xb[threadIdx.x] = make4<R>(px, py, pz);
     }
-    if (GRAD && t1 == A.T && lead) {
-        R* Gt = G + (long long)A.T * s;
+    if (GRAD && t1 == T && lead) {
+        R* Gt = G + (long long)T * s;
         Gt[i] = rpx * k.ginv;
         Gt[N + i] = rpy * k.ginv;
         Gt[2 * N + i] = rpz * k.ginv;
     }
     const double tot = block_sum(acc, red);
-    if (threadIdx.x == 0) A.partials[A.slot0 + chain * gridDim.x + tile] = tot;
+    if (threadIdx.x == 0) partials[I.slot] = tot;
 }
 
-size_t lj_smem_bytes(int N, int tpp, int maxnb, bool fp64)
+// Persistent grid: each CTA takes items from *counter until none is left.
+template <typename R, bool GRAD, int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
+    lj_action_kernel(const LJItem* __restrict__ items, int n_items,
+                     const LJSysDev<R>* __restrict__ systems, int nmax, const R* __restrict__ pos,
+                     R* __restrict__ grad, double* __restrict__ partials, int* __restrict__ counter)
 {
-    const int NT = ((N * tpp + 31) / 32) * 32;
-    const int cap = maxnb / tpp;
-    const size_t v4 = fp64 ? sizeof(double4a) : sizeof(float4);
-    return 3 * (size_t)N * v4 + (size_t)cap * NT * sizeof(uint16_t);
-}
-
-template <typename R, int TPP, bool GRAD>
-static cudaError_t launch_lj_t(const LJArgs<R>& A, int n_tiles, int n_chains, size_t smem,
-                               cudaStream_t st)
-{
-    const int NT = ((A.N * TPP + 31) / 32) * 32;
-    auto kern = NT <= 512 ? lj_action_kernel<R, TPP, GRAD, 512> : lj_action_kernel<R, TPP, GRAD, 1024>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<dim3(n_tiles, n_chains), NT, smem, st>>>(A);
-    return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_lj_action(const R* pos, R* grad, double* partials, int slot0, int N, int T,
-                             int n_chains, long long sys_offset, const LJConst& c, int tile_steps,
-                             int tpp, int maxnb, bool with_grad, cudaStream_t st)
-{
-    LJArgs<R> A;
-    A.pos = pos;
-    A.grad = grad;
-    A.partials = partials;
-    A.slot0 = slot0;
-    A.N = N;
-    A.T = T;
-    A.TS = tile_steps;
-    A.cap = maxnb / tpp;
-    A.sys_offset = sys_offset;
-    A.k = make_lj_consts<R>(c, 0.0);
-    const int n_tiles = (T + tile_steps - 1) / tile_steps;
-    const size_t smem = lj_smem_bytes(N, tpp, maxnb, sizeof(R) == 8);
-    if (n_tiles <= 0 || n_chains <= 0) return cudaSuccess;
-    switch (tpp) {
-        case 1: return with_grad ? launch_lj_t<R, 1, true>(A, n_tiles, n_chains, smem, st)
-                                 : launch_lj_t<R, 1, false>(A, n_tiles, n_chains, smem, st);
-        case 2: return with_grad ? launch_lj_t<R, 2, true>(A, n_tiles, n_chains, smem, st)
-                                 : launch_lj_t<R, 2, false>(A, n_tiles, n_chains, smem, st);
-        case 4: return with_grad ? launch_lj_t<R, 4, true>(A, n_tiles, n_chains, smem, st)
-                                 : launch_lj_t<R, 4, false>(A, n_tiles, n_chains, smem, st);
-        default: return cudaErrorInvalidValue;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const LJItem I = items[it];
+        const LJSysDev<R> S = systems[I.sys];
+        lj_item<R, GRAD>(I, S, smem_raw, nmax, pos, grad, partials, red);
     }
 }
 
-template cudaError_t launch_lj_action<float>(const float*, float*, double*, int, int, int, int,
-                                             long long, const LJConst&, int, int, int, bool,
+size_t lj_smem_bytes(int nmax, int NT, int cap_lane, bool fp64)
+{
+    const size_t v4 = fp64 ? sizeof(double4a) : sizeof(float4);
+    return 3 * (size_t)nmax * v4 + (size_t)cap_lane * NT * sizeof(uint16_t);
+}
+
+template <typename R, bool GRAD>
+static auto lj_kernel_ptr(int NT)
+{
+    return NT <= 512 ? lj_action_kernel<R, GRAD, 512> : lj_action_kernel<R, GRAD, 1024>;
+}
+
+template <typename R>
+int lj_blocks_per_sm(int NT, size_t smem, bool with_grad)
+{
+    auto kern = with_grad ? lj_kernel_ptr<R, true>(NT) : lj_kernel_ptr<R, false>(NT);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+template <typename R>
+cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_table, int nmax,
+                            const R* pos, R* grad, double* partials, int* counter, int NT,
+                            size_t smem, int grid, bool with_grad, cudaStream_t st)
+{
+    if (n_items <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    auto kern = with_grad ? lj_kernel_ptr<R, true>(NT) : lj_kernel_ptr<R, false>(NT);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, smem, st>>>(items, n_items, static_cast<const LJSysDev<R>*>(sys_table), nmax,
+                                 pos, grad, partials, counter);
+    return cudaGetLastError();
+}
+
+template int lj_blocks_per_sm<float>(int, size_t, bool);
+template int lj_blocks_per_sm<double>(int, size_t, bool);
+template cudaError_t launch_lj_items<float>(const LJItem*, int, const void*, int, const float*,
+                                            float*, double*, int*, int, size_t, int, bool,
+                                            cudaStream_t);
+template cudaError_t launch_lj_items<double>(const LJItem*, int, const void*, int, const double*,
+                                             double*, double*, int*, int, size_t, int, bool,
                                              cudaStream_t);
-template cudaError_t launch_lj_action<double>(const double*, double*, double*, int, int, int, int,
-                                              long long, const LJConst&, int, int, int, bool,
-                                              cudaStream_t);
 
 // ------------------------------------------------------------------ Euler-Maruyama (Eq. (2))
 // One CTA per chain, sequential in time; forces as in the action kernel.
-template <typename R, int TPP>
+template <typename R>
 __global__ void __launch_bounds__(1024)
-    lj_euler_kernel(R* __restrict__ pos, const R* __restrict__ noise, int N, int T,
-                    long long sys_offset, int chain0, int cap, const LJK<R> k, uint64_t seed,
-                    uint64_t counter)
+    lj_euler_kernel(R* __restrict__ pos, const R* __restrict__ noise, const LJSysDev<R> S,
+                    int chain0, uint64_t seed, uint64_t counter)
 {
     using V4 = vec4_t<R>;
     extern __shared__ __align__(32) unsigned char smem_raw[];
+    const int N = S.N, T = S.T;
     V4* xa = reinterpret_cast<V4*>(smem_raw);
     V4* xb = xa + N;
-    LJBlock<R, TPP> L;
-    L.N = N;
-    L.NT = blockDim.x;
-    L.tid = threadIdx.x;
-    L.i = threadIdx.x / TPP;
-    L.q = threadIdx.x % TPP;
-    L.active = L.i < N;
-    L.cap = cap;
-    L.nbr = reinterpret_cast<uint16_t*>(xb + 2 * N);  // same offset as the action kernel
+    LJBlock<R> L;
+    L.init(N, S.tpp, S.lg_tpp, S.cap, reinterpret_cast<uint16_t*>(xb + 2 * N));
+    const LJK<R>& k = S.k;
     const int chain = blockIdx.x, s = 3 * N, i = L.i;
-    const long long chain_len = (long long)(T + 1) * s;
-    R* X = pos + sys_offset + chain * chain_len;
-    const R* Z = noise ? noise + sys_offset + chain * chain_len : nullptr;
+    R* X = pos + S.off + chain * S.chain_len;
+    const R* Z = noise ? noise + S.off + chain * S.chain_len : nullptr;
     load_slice<R>(xa, X, N);
     __syncthreads();
     L.build(xa, k);
@@ -483,42 +448,25 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-template <typename R, int TPP>
-static cudaError_t launch_lj_euler_t(R* pos, const R* noise, int N, int T, int n_chains,
-                                     long long sys_offset, int chain0, int cap, const LJK<R>& k,
-                                     uint64_t seed, uint64_t counter, size_t smem, cudaStream_t st)
+template <typename R>
+cudaError_t launch_lj_euler(R* pos, const R* noise, const void* sys_entry_host, int NT, size_t smem,
+                            int n_chains, int chain0, uint64_t seed, uint64_t counter,
+                            cudaStream_t st)
 {
-    auto kern = lj_euler_kernel<R, TPP>;
+    if (n_chains <= 0) return cudaSuccess;
+    const LJSysDev<R> S = *static_cast<const LJSysDev<R>*>(sys_entry_host);
+    if (S.T <= 0) return cudaSuccess;
+    auto kern = lj_euler_kernel<R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int NT = ((N * TPP + 31) / 32) * 32;
-    kern<<<n_chains, NT, smem, st>>>(pos, noise, N, T, sys_offset, chain0, cap, k, seed, counter);
+    kern<<<n_chains, NT, smem, st>>>(pos, noise, S, chain0, seed, counter);
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_lj_euler(R* pos, const R* noise, int N, int T, int n_chains, long long sys_offset,
-                            int chain0, const LJConst& c, int tpp, int maxnb, double sig,
-                            uint64_t seed, uint64_t counter, cudaStream_t st)
-{
-    if (n_chains <= 0 || T <= 0) return cudaSuccess;
-    const LJK<R> k = make_lj_consts<R>(c, sig);
-    const size_t smem = lj_smem_bytes(N, tpp, maxnb, sizeof(R) == 8);
-    const int cap = maxnb / tpp;
-    switch (tpp) {
-        case 1: return launch_lj_euler_t<R, 1>(pos, noise, N, T, n_chains, sys_offset, chain0, cap, k, seed, counter, smem, st);
-        case 2: return launch_lj_euler_t<R, 2>(pos, noise, N, T, n_chains, sys_offset, chain0, cap, k, seed, counter, smem, st);
-        case 4: return launch_lj_euler_t<R, 4>(pos, noise, N, T, n_chains, sys_offset, chain0, cap, k, seed, counter, smem, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template cudaError_t launch_lj_euler<float>(float*, const float*, int, int, int, long long, int,
-                                            const LJConst&, int, int, double, uint64_t, uint64_t,
-                                            cudaStream_t);
-template cudaError_t launch_lj_euler<double>(double*, const double*, int, int, int, long long, int,
-                                             const LJConst&, int, int, double, uint64_t, uint64_t,
-                                             cudaStream_t);
+template cudaError_t launch_lj_euler<float>(float*, const float*, const void*, int, size_t, int, int,
+                                            uint64_t, uint64_t, cudaStream_t);
+template cudaError_t launch_lj_euler<double>(double*, const double*, const void*, int, size_t, int,
+                                             int, uint64_t, uint64_t, cudaStream_t);
 
 // ------------------------------------------------------------------ pair-count diagnostic
 // Ordered in-cutoff pairs per slice, single-precision rule, all pairs.

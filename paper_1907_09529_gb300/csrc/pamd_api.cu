@@ -4,7 +4,9 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -30,6 +32,7 @@ struct LJTune {
 };
 
 LJTune g_tune_override;  // 0 / negative fields mean "automatic"
+constexpr int kMaxListPerThread = 1024;  // list entries per thread (uint16 indices)
 std::mutex g_mutex;
 
 struct SysInfo {
@@ -37,6 +40,7 @@ struct SysInfo {
     long long off, chain_len;
     pamd_potential pot;
     LJTune tune;       // LJ only
+    int lj_index = -1; // row in the LJ system table
     int slot0 = 0;     // first S slot (LJ tiles)
     int n_tiles = 0;
 };
@@ -69,6 +73,16 @@ struct Plan {
     double* d_part_S = nullptr;
     double* d_part_qf = nullptr;
     double* d_part_qr = nullptr;
+    // LJ work items (persistent kernel)
+    int lj_NT = 0, lj_nmax = 0, lj_grid_grad = 0, lj_grid_nograd = 0;
+    size_t lj_smem = 0;
+    std::vector<unsigned char> h_lj_sys;  // host copy of the system table
+    size_t lj_sys_stride = 0;
+    void* d_lj_sys = nullptr;
+    LJItem* d_lj_items = nullptr;
+    int n_lj_items = 0;
+    std::vector<int> lj_chain_first, lj_chain_count;  // per global chain (plain form)
+    int* d_counter = nullptr;
     // update workspace (allocated on first use)
     void* d_prop = nullptr;
     void* d_gprop = nullptr;
@@ -138,7 +152,8 @@ std::string plan_key(const pamd_problem* p)
 {
     std::ostringstream os;
     os.precision(17);
-    os << p->precision << '|' << p->flags << '|' << p->n_systems << '|' << g_tune_override.tile_steps
+    os << p->precision << '|' << p->flags << '|' << p->D << ',' << p->beta << ',' << p->dt << '|'
+       << p->n_systems << '|' << g_tune_override.tile_steps
        << ',' << g_tune_override.tpp << ',' << g_tune_override.maxnb << ',' << g_tune_override.skin;
     for (int q = 0; q < p->n_systems; ++q) {
         const pamd_system& s = p->systems[q];
@@ -158,32 +173,74 @@ int max_dynamic_smem()
     return v;
 }
 
-// Default LJ launch shape: threads per particle (N * tpp <= 512 where possible,
-// so that two CTAs share an SM), Verlet skin, list capacity, tile length.
-LJTune choose_lj_tune(const pamd_system& s, bool fp64)
+// Block size shared by every LJ system of a problem: the largest N rounded up
+// to a warp multiple (at least 128); blocks of <= 512 threads run two per SM.
+int choose_lj_block(const pamd_problem* p)
+{
+    int nmax = 0;
+    for (int q = 0; q < p->n_systems; ++q)
+        if (p->systems[q].pot.kind == PAMD_LJ) nmax = std::max(nmax, p->systems[q].n_particles);
+    int NT = std::max(128, ((nmax + 31) / 32) * 32);
+    if (g_tune_override.tpp > 0) NT = std::max(NT, std::min(1024, ((nmax * g_tune_override.tpp + 31) / 32) * 32));
+    return NT;
+}
+
+// Per-system LJ launch shape: threads per particle (largest power of two <= 8
+// with N * tpp <= NT), Verlet skin, list capacity per thread, tile length.
+LJTune choose_lj_tune(const pamd_system& s, int NT, int cap_lane_max)
 {
     LJTune t;
     const int N = s.n_particles;
-    if (fp64)  // double precision: more threads per particle (latency of FP64 math)
-        t.tpp = g_tune_override.tpp > 0 ? g_tune_override.tpp : (N <= 256 ? 4 : (N <= 512 ? 2 : 1));
-    else
-        t.tpp = g_tune_override.tpp > 0 ? g_tune_override.tpp : (N <= 128 ? 4 : (N <= 256 ? 2 : 1));
-    while (t.tpp > 1 && N * t.tpp > 1024) t.tpp >>= 1;
-    t.skin = g_tune_override.skin >= 0 ? g_tune_override.skin : 0.25;
+    int tpp = 1;
+    while (tpp < 8 && N * tpp * 2 <= NT) tpp *= 2;
+    if (g_tune_override.tpp > 0) {
+        const int lim = std::min(g_tune_override.tpp, std::max(1, NT / N));
+        tpp = 1;
+        while (tpp * 2 <= lim) tpp *= 2;  // a power of two (lane = tid mod tpp)
+    }
+    while (tpp > 1 && N * tpp > NT) tpp >>= 1;
+    t.tpp = tpp;
+    t.skin = g_tune_override.skin >= 0 ? g_tune_override.skin : 0.3;
     t.tile_steps = g_tune_override.tile_steps > 0 ? g_tune_override.tile_steps : 32;
     const double L = s.pot.box, rho = N / (L * L * L), rl = s.pot.rc + t.skin;
     const double expect = 4.18879020478639 * rl * rl * rl * rho;  // 4/3 pi rl^3 rho
     int want = (int)(1.2 * expect) + 8;
-    if (want > N - 1 + t.tpp) want = N - 1 + t.tpp;
+    if (want > N - 1 + tpp) want = N - 1 + tpp;
     if (g_tune_override.maxnb > 0) want = g_tune_override.maxnb;
-    want = ((want + t.tpp - 1) / t.tpp) * t.tpp;
-    // shrink until it fits: two CTAs per SM for blocks of <= 512 threads
-    const int NT = ((N * t.tpp + 31) / 32) * 32;
-    const int smax = (NT <= 512 && !fp64 && g_tune_override.maxnb <= 0) ? 113 * 1024
-                                                                        : max_dynamic_smem() - 1024;
-    while (want > t.tpp && (int)lj_smem_bytes(N, t.tpp, want, fp64) > smax) want -= t.tpp;
-    t.maxnb = want;
+    int lane = (want + tpp - 1) / tpp;
+    t.maxnb = std::max(1, std::min(std::min(lane, cap_lane_max), kMaxListPerThread));  // per thread
     return t;
+}
+
+template <typename R>
+void fill_lj_sys(Plan* P, const pamd_problem* p)
+{
+    P->lj_sys_stride = sizeof(LJSysDev<R>);
+    int nlj = 0;
+    for (auto& si : P->sys) nlj += si.kind == PAMD_LJ;
+    P->h_lj_sys.assign(P->lj_sys_stride * std::max(nlj, 1), 0);
+    for (auto& si : P->sys) {
+        if (si.kind != PAMD_LJ) continue;
+        LJSysDev<R> d;
+        d.off = si.off;
+        d.chain_len = si.chain_len;
+        d.N = si.N;
+        d.T = si.T;
+        d.tpp = si.tune.tpp;
+        d.lg_tpp = 0;
+        while ((1 << d.lg_tpp) < d.tpp) ++d.lg_tpp;
+        d.cap = si.tune.maxnb;
+        LJConst c;
+        c.L = si.pot.box;
+        c.rc = si.pot.rc;
+        c.eps = si.pot.eps;
+        c.sigma = si.pot.sigma;
+        c.a = p->beta * p->D * p->dt;
+        c.ginv = 1.0 / (2.0 * p->D * p->dt);
+        c.skin = si.tune.skin;
+        d.k = make_lj_consts<R>(c, std::sqrt(2.0 * p->D * p->dt));
+        std::memcpy(&P->h_lj_sys[P->lj_sys_stride * si.lj_index], &d, sizeof(d));
+    }
 }
 
 int build_plan(const pamd_problem* p, Plan** out)
@@ -212,7 +269,6 @@ int build_plan(const pamd_problem* p, Plan** out)
         si.off = s.pos_offset;
         si.chain_len = (long long)(s.n_steps + 1) * s.dim * s.n_particles;
         si.pot = s.pot;
-        if (si.kind == PAMD_LJ) si.tune = choose_lj_tune(s, P->fp64);
         P->span = std::max(P->span, si.off + si.chain_len * si.chains);
         P->sys.push_back(si);
         chain += s.n_chains;
@@ -254,16 +310,92 @@ int build_plan(const pamd_problem* p, Plan** out)
         }
     }
     int slot = (int)P->h_ho.size();
-    for (auto& si : P->sys) {
-        if (si.kind != PAMD_LJ) continue;
-        si.n_tiles = (si.T + si.tune.tile_steps - 1) / si.tune.tile_steps;
-        si.slot0 = slot;
-        for (int b = 0; b < si.chains; ++b) {
-            Sslots[si.chain0 + b].begin = slot + b * si.n_tiles;
-            Sslots[si.chain0 + b].end = slot + (b + 1) * si.n_tiles;
+    // LJ: common block size, shared-memory budget, per-system shapes, items.
+    std::vector<LJItem> items;
+    P->lj_chain_first.assign(chain, -1);
+    P->lj_chain_count.assign(chain, 0);
+    {
+        const bool one = (p->flags & PAMD_FLAG_ONE_CHAIN_PER_LAUNCH) != 0;
+        int nlj = 0, nmax = 0;
+        for (auto& si : P->sys)
+            if (si.kind == PAMD_LJ) {
+                si.lj_index = nlj++;
+                nmax = std::max(nmax, si.N);
+            }
+        if (nlj) {
+            const int NT = choose_lj_block(p);
+            const size_t v4 = P->fp64 ? 32 : 16;
+            const int budget = (NT <= 512 && !P->fp64 && g_tune_override.maxnb <= 0)
+                                   ? 113 * 1024
+                                   : max_dynamic_smem() - 1024;
+            const int cap_lane_max =
+                std::max(1, (int)((budget - 3 * (long long)nmax * v4) / (2 * (long long)NT)));
+            int cap_used = 1;
+            std::vector<double> cost;
+            for (int q = 0; q < (int)P->sys.size(); ++q) {
+                SysInfo& si = P->sys[q];
+                if (si.kind != PAMD_LJ) continue;
+                si.tune = choose_lj_tune(p->systems[q], NT, cap_lane_max);
+                cap_used = std::max(cap_used, si.tune.maxnb);
+                si.n_tiles = (si.T + si.tune.tile_steps - 1) / si.tune.tile_steps;
+                si.slot0 = slot;
+                for (int b = 0; b < si.chains; ++b) {
+                    const int c = si.chain0 + b;
+                    Sslots[c].begin = slot + b * si.n_tiles;
+                    Sslots[c].end = slot + (b + 1) * si.n_tiles;
+                    P->lj_chain_first[c] = (int)items.size();
+                    P->lj_chain_count[c] = si.n_tiles;
+                    for (int tl = 0; tl < si.n_tiles; ++tl) {
+                        LJItem it;
+                        it.sys = si.lj_index;
+                        it.chain = b;
+                        it.t0 = tl * si.tune.tile_steps;
+                        it.t1 = std::min(si.T, it.t0 + si.tune.tile_steps);
+                        it.slot = slot + b * si.n_tiles + tl;
+                        items.push_back(it);
+                        cost.push_back((double)si.N * si.tune.maxnb * si.tune.tpp * (it.t1 - it.t0 + 1));
+                    }
+                }
+                slot += si.chains * si.n_tiles;
+            }
+            if (!one) {  // largest items first
+                std::vector<int> ord(items.size());
+                for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+                std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+                std::vector<LJItem> sorted;
+                for (int q : ord) sorted.push_back(items[q]);
+                items.swap(sorted);
+            }
+            P->lj_NT = NT;
+            P->lj_nmax = nmax;
+            P->lj_smem = lj_smem_bytes(nmax, NT, cap_used, P->fp64);
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int bg = P->fp64 ? lj_blocks_per_sm<double>(NT, P->lj_smem, true)
+                                   : lj_blocks_per_sm<float>(NT, P->lj_smem, true);
+            const int bn = P->fp64 ? lj_blocks_per_sm<double>(NT, P->lj_smem, false)
+                                   : lj_blocks_per_sm<float>(NT, P->lj_smem, false);
+            if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
+            P->lj_grid_grad = std::max(1, std::min((int)items.size(), bg * sms));
+            P->lj_grid_nograd = std::max(1, std::min((int)items.size(), bn * sms));
+            if (P->fp64)
+                fill_lj_sys<double>(P.get(), p);
+            else
+                fill_lj_sys<float>(P.get(), p);
+            if (std::getenv("PAMD_DEBUG_PLAN")) {
+                std::fprintf(stderr, "pamd plan: NT=%d nmax=%d smem=%zu blocks/SM grad=%d nograd=%d "
+                             "grid=%d items=%zu\n", NT, nmax, P->lj_smem, bg, bn, P->lj_grid_grad,
+                             items.size());
+                for (auto& si : P->sys)
+                    if (si.kind == PAMD_LJ)
+                        std::fprintf(stderr, "  N=%d T=%d tpp=%d cap/thread=%d skin=%.3f tile=%d\n",
+                                     si.N, si.T, si.tune.tpp, si.tune.maxnb, si.tune.skin,
+                                     si.tune.tile_steps);
+            }
         }
-        slot += si.chains * si.n_tiles;
     }
+    P->n_lj_items = (int)items.size();
     P->n_S_slots = slot;
     int rc;
     if ((rc = P->alloc(&P->d_all, sizeof(ElemBlock) * P->h_all.size()))) return rc;
@@ -273,6 +405,15 @@ int build_plan(const pamd_problem* p, Plan** out)
     if ((rc = P->alloc(&P->d_part_S, sizeof(double) * P->n_S_slots))) return rc;
     if ((rc = P->alloc(&P->d_part_qf, sizeof(double) * P->h_all.size()))) return rc;
     if ((rc = P->alloc(&P->d_part_qr, sizeof(double) * P->h_all.size()))) return rc;
+    if ((rc = P->alloc(&P->d_lj_items, sizeof(LJItem) * items.size()))) return rc;
+    if ((rc = P->alloc(&P->d_lj_sys, P->h_lj_sys.size()))) return rc;
+    if ((rc = P->alloc(&P->d_counter, sizeof(int)))) return rc;
+    if (!items.empty())
+        PAMD_CUDA_TRY(cudaMemcpy(P->d_lj_items, items.data(), sizeof(LJItem) * items.size(),
+                                 cudaMemcpyHostToDevice));
+    if (!P->h_lj_sys.empty())
+        PAMD_CUDA_TRY(cudaMemcpy(P->d_lj_sys, P->h_lj_sys.data(), P->h_lj_sys.size(),
+                                 cudaMemcpyHostToDevice));
     if (!P->h_all.empty())
         PAMD_CUDA_TRY(cudaMemcpy(P->d_all, P->h_all.data(), sizeof(ElemBlock) * P->h_all.size(),
                                  cudaMemcpyHostToDevice));
@@ -315,19 +456,6 @@ bool is_host_ptr(const void* ptr)
     return !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
 }
 
-LJConst lj_const(const pamd_problem* p, const SysInfo& si)
-{
-    LJConst c;
-    c.L = si.pot.box;
-    c.rc = si.pot.rc;
-    c.eps = si.pot.eps;
-    c.sigma = si.pot.sigma;
-    c.a = p->beta * p->D * p->dt;
-    c.ginv = 1.0 / (2.0 * p->D * p->dt);
-    c.skin = si.tune.skin;
-    return c;
-}
-
 // S (and grad) of every chain into S_out, from device pointers.
 template <typename R>
 int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_out, bool with_grad,
@@ -348,19 +476,21 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
             }
         }
     }
-    for (const auto& si : P->sys) {
-        if (si.kind != PAMD_LJ) continue;
-        const LJConst c = lj_const(p, si);
+    if (P->n_lj_items > 0) {
+        const int grid = with_grad ? P->lj_grid_grad : P->lj_grid_nograd;
         if (!one) {
-            PAMD_CUDA_TRY(launch_lj_action<R>(pos, grad, P->d_part_S, si.slot0, si.N, si.T, si.chains,
-                                              si.off, c, si.tune.tile_steps, si.tune.tpp,
-                                              si.tune.maxnb, with_grad, st));
+            PAMD_CUDA_TRY(launch_lj_items<R>(P->d_lj_items, P->n_lj_items, P->d_lj_sys, P->lj_nmax, pos,
+                                             grad, P->d_part_S, P->d_counter, P->lj_NT, P->lj_smem,
+                                             grid, with_grad, st));
         } else {
-            for (int b = 0; b < si.chains; ++b)
-                PAMD_CUDA_TRY(launch_lj_action<R>(pos, grad, P->d_part_S, si.slot0 + b * si.n_tiles,
-                                                  si.N, si.T, 1, si.off + b * si.chain_len, c,
-                                                  si.tune.tile_steps, si.tune.tpp, si.tune.maxnb,
-                                                  with_grad, st));
+            for (int c = 0; c < P->n_chains; ++c) {
+                const int f = P->lj_chain_first[c];
+                if (f < 0) continue;
+                const int n = P->lj_chain_count[c];
+                PAMD_CUDA_TRY(launch_lj_items<R>(P->d_lj_items + f, n, P->d_lj_sys, P->lj_nmax, pos,
+                                                 grad, P->d_part_S, P->d_counter, P->lj_NT, P->lj_smem,
+                                                 std::min(grid, n), with_grad, st));
+            }
         }
     }
     PAMD_CUDA_TRY(launch_finalize(P->d_part_S, P->d_S_slots, P->n_chains, 1.0 / (4.0 * p->D * p->dt),
@@ -634,15 +764,16 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
                                                      si.T, si.chains, si.off, si.chain0, si.pot.k, a,
                                                      sig, seed, counter, st));
         } else {
-            const LJConst c = lj_const(prob, si);
+            const void* row = &P->h_lj_sys[P->lj_sys_stride * si.lj_index];
+            const size_t smem = lj_smem_bytes(si.N, P->lj_NT, si.tune.maxnb, P->fp64);
             if (P->fp64)
-                PAMD_CUDA_TRY(launch_lj_euler<double>((double*)dpos, (const double*)dnoise, si.N, si.T,
-                                                      si.chains, si.off, si.chain0, c, si.tune.tpp,
-                                                      si.tune.maxnb, sig, seed, counter, st));
+                PAMD_CUDA_TRY(launch_lj_euler<double>((double*)dpos, (const double*)dnoise, row,
+                                                      P->lj_NT, smem, si.chains, si.chain0, seed,
+                                                      counter, st));
             else
-                PAMD_CUDA_TRY(launch_lj_euler<float>((float*)dpos, (const float*)dnoise, si.N, si.T,
-                                                     si.chains, si.off, si.chain0, c, si.tune.tpp,
-                                                     si.tune.maxnb, sig, seed, counter, st));
+                PAMD_CUDA_TRY(launch_lj_euler<float>((float*)dpos, (const float*)dnoise, row,
+                                                     P->lj_NT, smem, si.chains, si.chain0, seed,
+                                                     counter, st));
         }
     }
     if (host) {

@@ -164,14 +164,76 @@ struct LJConst {
     double L, rc, eps, sigma, a, ginv, skin;
 };
 
-// LJ action (+ gradient) of one system: grid (tiles, chains).
+// Per-system constants of the LJ kernels in the element type.
 template <typename R>
-cudaError_t launch_lj_action(const R* pos, R* grad, double* partials, int slot0, int N, int T,
-                             int n_chains, long long sys_offset, const LJConst& c, int tile_steps,
-                             int tpp, int maxnb, bool with_grad, cudaStream_t st);
+struct LJK {
+    R L, iL, rc2, rl2, hs2;  // box, 1/box, rc^2, list radius^2, (skin/2)^2
+    R c1, c2, c3, duc;       // 24 eps sigma^6, 2 sigma^6, 26 sigma^6, u'(rc)
+    R a, ginv, sig_em;       // beta D dt, 1/(2 D dt), sqrt(2 D dt)
+};
 
-// Shared memory the LJ kernel needs for (N, tpp, maxnb).
-size_t lj_smem_bytes(int N, int tpp, int maxnb, bool fp64);
+template <typename R>
+inline LJK<R> make_lj_consts(const LJConst& c, double sig_em)
+{
+    LJK<R> k;
+    const double rl = c.rc + c.skin;
+    const double s6 = c.sigma * c.sigma * c.sigma * c.sigma * c.sigma * c.sigma;
+    const double src = c.sigma / c.rc;
+    const double q6 = src * src * src * src * src * src;
+    // u'(rc) = 4 eps (-12 (s/rc)^12 + 6 (s/rc)^6) / rc
+    const double duc = 4.0 * c.eps * (-12.0 * q6 * q6 + 6.0 * q6) / c.rc;
+    if (sizeof(R) == sizeof(float)) {
+        // The single-precision cutoff rule: L, 1/L and rc^2 rounded to float.
+        const float Lf = (float)c.L;
+        const float rcf = (float)c.rc;
+        k.L = (R)Lf;
+        k.iL = (R)(1.0f / Lf);
+        k.rc2 = (R)(rcf * rcf);
+    } else {
+        k.L = (R)c.L;
+        k.iL = (R)(1.0 / c.L);
+        k.rc2 = (R)(c.rc * c.rc);
+    }
+    k.rl2 = (R)(rl * rl);
+    k.hs2 = (R)(0.25 * c.skin * c.skin);
+    k.c1 = (R)(24.0 * c.eps * s6);
+    k.c2 = (R)(2.0 * s6);
+    k.c3 = (R)(26.0 * s6);
+    k.duc = (R)duc;
+    k.a = (R)c.a;
+    k.ginv = (R)c.ginv;
+    k.sig_em = (R)sig_em;
+    return k;
+}
+
+// One LJ system as the kernels see it.
+template <typename R>
+struct LJSysDev {
+    long long off;        // element offset of chain 0
+    long long chain_len;  // (T+1) * 3N
+    int N, T;
+    int tpp, lg_tpp;      // threads per particle (power of two) and its log2
+    int cap;              // neighbour-list capacity per thread
+    LJK<R> k;
+};
+
+// A work item: steps [t0, t1) of one chain of one system; its |r|^2 sum goes
+// to partials[slot].
+struct LJItem {
+    int sys, chain, t0, t1, slot;
+};
+
+// Shared memory of the LJ action kernel: three slices of nmax particles and a
+// list of cap_lane entries for each of NT threads.
+size_t lj_smem_bytes(int nmax, int NT, int cap_lane, bool fp64);
+
+template <typename R>
+int lj_blocks_per_sm(int NT, size_t smem, bool with_grad);
+
+template <typename R>
+cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_table, int nmax,
+                            const R* pos, R* grad, double* partials, int* counter, int NT,
+                            size_t smem, int grid, bool with_grad, cudaStream_t st);
 
 cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, int T, int n_chains,
                                   long long sys_offset, double L, double rc, cudaStream_t st);
@@ -182,9 +244,9 @@ cudaError_t launch_ho_euler(R* pos, const R* noise, int s, int T, int n_chains, 
                             int chain0, double k, double a, double sig, uint64_t seed,
                             uint64_t counter, cudaStream_t st);
 template <typename R>
-cudaError_t launch_lj_euler(R* pos, const R* noise, int N, int T, int n_chains, long long sys_offset,
-                            int chain0, const LJConst& c, int tpp, int maxnb, double sig,
-                            uint64_t seed, uint64_t counter, cudaStream_t st);
+cudaError_t launch_lj_euler(R* pos, const R* noise, const void* sys_entry_host, int NT, size_t smem,
+                            int n_chains, int chain0, uint64_t seed, uint64_t counter,
+                            cudaStream_t st);
 
 // Deterministic per-chain sums of partials: out[c] = scale * sum(partials[slots[c]]).
 cudaError_t launch_finalize(const double* partials, const ChainSlots* slots, int n_chains,
