@@ -34,7 +34,9 @@
  * is a host pointer, the library copies inputs to its own device workspace,
  * runs, copies results back, and synchronises `stream` before returning.
  * With device pointers every call is asynchronous on `stream`.  Device
- * buffers must be 16-byte aligned.
+ * buffers must be 16-byte aligned, and are read in whole 16-byte units: a
+ * buffer must stay readable up to its end rounded up to 16 bytes (any
+ * cudaMalloc'd buffer is).
  *
  * Errors.  Every entry point returns PAMD_OK (0) or a negative status; no
  * C++ exception crosses this boundary.  On error nothing is guaranteed
@@ -180,6 +182,12 @@ int pamd_philox(uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3, uint
  *   out : float[n], written. */
 int pamd_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain,
                  long long e0, long long n, float* out, void* stream);
+
+/* Status left on the device by earlier asynchronous calls: synchronises
+ * `stream`, then returns PAMD_ERR_NONFINITE (and clears it) if an action
+ * computed since the last check was not finite (overlapping particles, an
+ * exploding path), else PAMD_OK. */
+int pamd_device_status(void* stream);
 
 /* Launch-shape override for the Lennard-Jones kernels (0 or a negative skin
  * keeps the automatic choice): steps per CTA tile, threads per particle

@@ -17,7 +17,7 @@ import torch
 
 from . import _lib
 from ._lib import (PAMD_FLAG_ONE_CHAIN_PER_LAUNCH, PAMD_FP32, PAMD_FP64, PAMD_HARMONIC, PAMD_LJ,
-                   PamdError, pamd_action, pamd_action_grad, pamd_euler_reference,
+                   PamdError, pamd_action, pamd_action_grad, pamd_device_status, pamd_euler_reference,
                    pamd_lj_pair_counts, pamd_normals, pamd_path_update, pamd_philox,
                    pamd_release_cache, pamd_tune, pamd_version)
 
@@ -26,7 +26,7 @@ __all__ = [
     "lj_pair_counts", "philox", "normals", "PamdAction", "PamdError", "tune", "release_cache",
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_release_cache", "pamd_tune",
-    "pamd_version",
+    "pamd_version", "pamd_device_status", "device_status",
 ]
 
 ALIGN = 8  # system offsets are rounded to 8 elements (>= 16 bytes)
@@ -189,6 +189,12 @@ def tune(tile_steps: int = 0, threads_per_particle: int = 0, max_neighbours: int
 
 def release_cache():
     pamd_release_cache()
+
+
+def device_status(stream=None):
+    """Raise PamdError if an action computed since the last check was not finite."""
+    s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+    pamd_device_status(s)
 
 
 class PamdAction(torch.autograd.Function):

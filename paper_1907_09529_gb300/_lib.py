@@ -32,6 +32,7 @@ EXPORTS = (
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
+    "pamd_device_status",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
             "pamd_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double]),
             "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
+            "pamd_device_status": (ctypes.c_int, [_VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -149,6 +151,10 @@ def pamd_normals(seed, counter, stream_id, chain, e0, n, out, stream):
 
 def pamd_tune(tile_steps, threads_per_particle, max_neighbours, skin):
     return _call("pamd_tune", tile_steps, threads_per_particle, max_neighbours, skin)
+
+
+def pamd_device_status(stream):
+    return _call("pamd_device_status", stream)
 
 
 def pamd_release_cache():

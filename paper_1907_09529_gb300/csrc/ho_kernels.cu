@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(kElemThreads)
     ho_action_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
                      R* __restrict__ grad, double* __restrict__ partials, int slot0, R a, R ginv)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     R* xs = reinterpret_cast<R*>(smem_raw);
     __shared__ double red[kElemThreads / 32];
 
@@ -77,6 +77,93 @@ template cudaError_t launch_ho_action<float>(const ElemBlock*, int, int, const f
                                              double*, int, double, double, bool, cudaStream_t);
 template cudaError_t launch_ho_action<double>(const ElemBlock*, int, int, const double*, double*,
                                               double*, int, double, double, bool, cudaStream_t);
+
+// ------------------------------------------------------------------ vectorised form (s <= 4)
+// When a slice holds at most 4 elements (one particle in 1-3D, or a few in 1D),
+// the time neighbours e - s and e + s of the 4 elements in an aligned float4
+// all lie in the float4s just before and after it.  Each thread loads those
+// three 16-byte vectors (the neighbours' loads hit L1), forms 4 gradients in
+// registers and stores one float4: no shared-memory staging and no barrier
+// before the final block sum.  The unaligned ends of a block (< 4 elements
+// each) are done element by element.
+template <int S, bool GRAD>
+__global__ void __launch_bounds__(kElemThreads)
+    ho_vec_kernel(const ElemBlock* __restrict__ blocks, const float* __restrict__ pos,
+                  float* __restrict__ grad, double* __restrict__ partials, int slot0, float a,
+                  float ginv, long long sys_lo, long long sys_hi)
+{
+    __shared__ double red[kElemThreads / 32];
+    const ElemBlock B = blocks[blockIdx.x];
+    const float ak = a * (float)B.k;
+    const long long base = B.chain_base;
+    const long long glo = base + B.e0, ghi = glo + B.n;
+    const long long gal = (glo + 3) & ~3LL, gah = ghi & ~3LL;
+    const int rend = B.chain_len - S;
+    float acc = 0.f;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long g = gal + 4LL * threadIdx.x; g < gah; g += 4LL * kElemThreads) {
+        const float4 c = __ldg(reinterpret_cast<const float4*>(pos + g));
+        const float4 p = (g - 4 >= sys_lo) ? __ldg(reinterpret_cast<const float4*>(pos + g - 4)) : z4;
+        const float4 n = (g + 4 < sys_hi) ? __ldg(reinterpret_cast<const float4*>(pos + g + 4)) : z4;
+        const float xx[12] = {p.x, p.y, p.z, p.w, c.x, c.y, c.z, c.w, n.x, n.y, n.z, n.w};
+        float out[4];
+        const int le0 = (int)(g - base);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int le = le0 + l;
+            const float xm = xx[4 + l - S], x0 = xx[4 + l], xp = xx[4 + l + S];
+            const float rp = (le >= S) ? fma_r(ak, xm, x0 - xm) : 0.f;
+            const float r = (le < rend) ? fma_r(ak, x0, xp - x0) : 0.f;
+            out[l] = fma_r(ak, r, rp - r) * ginv;
+            acc = fma_r(r, r, acc);
+        }
+        if (GRAD)
+            *reinterpret_cast<float4*>(grad + g) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    // unaligned ends: [glo, gal) and [gah, ghi) (at most 3 + 3 elements), or the
+    // whole block (fewer than 8 elements) when it holds no aligned float4
+    const bool body = gal < gah;
+    const int nhead = (int)((body ? gal : ghi) - glo);
+    const int ntail = body ? (int)(ghi - gah) : 0;
+    if ((int)threadIdx.x < nhead + ntail) {
+        const long long g = (int)threadIdx.x < nhead ? glo + threadIdx.x : gah + (threadIdx.x - nhead);
+        const int le = (int)(g - base);
+        const float x0 = pos[g];
+        const float xm = le >= S ? pos[g - S] : 0.f;
+        const float xp = le < rend ? pos[g + S] : 0.f;
+        const float rp = (le >= S) ? fma_r(ak, xm, x0 - xm) : 0.f;
+        const float r = (le < rend) ? fma_r(ak, x0, xp - x0) : 0.f;
+        if (GRAD) grad[g] = fma_r(ak, r, rp - r) * ginv;
+        acc = fma_r(r, r, acc);
+    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) partials[slot0 + blockIdx.x] = tot;
+}
+
+template <int S>
+static cudaError_t launch_vec_s(const ElemBlock* blocks, int n_blocks, const float* pos, float* grad,
+                                double* partials, int slot0, double a, double ginv, bool with_grad,
+                                long long sys_lo, long long sys_hi, cudaStream_t st)
+{
+    auto kern = with_grad ? ho_vec_kernel<S, true> : ho_vec_kernel<S, false>;
+    kern<<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, grad, partials, slot0, (float)a, (float)ginv,
+                                            sys_lo, sys_hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ho_action_vec(const ElemBlock* blocks, int n_blocks, int s, const float* pos,
+                                 float* grad, double* partials, int slot0, double a, double ginv,
+                                 bool with_grad, long long sys_lo, long long sys_hi, cudaStream_t st)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    switch (s) {
+        case 1: return launch_vec_s<1>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
+        case 2: return launch_vec_s<2>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
+        case 3: return launch_vec_s<3>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
+        case 4: return launch_vec_s<4>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // ------------------------------------------------------------------ Euler-Maruyama (Eq. (2))
 // One thread per (chain, coordinate), sequential in time:

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <type_traits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -41,6 +42,7 @@ struct SysInfo {
     pamd_potential pot;
     LJTune tune;       // LJ only
     int lj_index = -1; // row in the LJ system table
+    int ho_b0 = 0, ho_b1 = 0;  // harmonic: range of this system's element blocks
     int slot0 = 0;     // first S slot (LJ tiles)
     int n_tiles = 0;
 };
@@ -83,6 +85,7 @@ struct Plan {
     int n_lj_items = 0;
     std::vector<int> lj_chain_first, lj_chain_count;  // per global chain (plain form)
     int* d_counter = nullptr;
+    int* d_err = nullptr;  // device status word (PAMD_OK or PAMD_ERR_NONFINITE)
     // update workspace (allocated on first use)
     void* d_prop = nullptr;
     void* d_gprop = nullptr;
@@ -285,6 +288,7 @@ int build_plan(const pamd_problem* p, Plan** out)
             const int c = si.chain0 + b;
             Eslots[c].begin = (int)P->h_all.size();
             if (si.kind == PAMD_HARMONIC) {
+                if (b == 0) si.ho_b0 = (int)P->h_ho.size();
                 Sslots[c].begin = (int)P->h_ho.size();
                 P->ho_chain_first[c] = (int)P->h_ho.size();
             }
@@ -303,6 +307,7 @@ int build_plan(const pamd_problem* p, Plan** out)
             }
             Eslots[c].end = (int)P->h_all.size();
             if (si.kind == PAMD_HARMONIC) {
+                si.ho_b1 = (int)P->h_ho.size();
                 Sslots[c].end = (int)P->h_ho.size();
                 P->ho_chain_count[c] = Sslots[c].end - Sslots[c].begin;
                 P->max_s_ho = std::max(P->max_s_ho, s);
@@ -408,6 +413,8 @@ int build_plan(const pamd_problem* p, Plan** out)
     if ((rc = P->alloc(&P->d_lj_items, sizeof(LJItem) * items.size()))) return rc;
     if ((rc = P->alloc(&P->d_lj_sys, P->h_lj_sys.size()))) return rc;
     if ((rc = P->alloc(&P->d_counter, sizeof(int)))) return rc;
+    if ((rc = P->alloc(&P->d_err, sizeof(int)))) return rc;
+    PAMD_CUDA_TRY(cudaMemset(P->d_err, 0, sizeof(int)));
     if (!items.empty())
         PAMD_CUDA_TRY(cudaMemcpy(P->d_lj_items, items.data(), sizeof(LJItem) * items.size(),
                                  cudaMemcpyHostToDevice));
@@ -463,17 +470,21 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
 {
     const double a = p->beta * p->D * p->dt, ginv = 1.0 / (2.0 * p->D * p->dt);
     const bool one = (p->flags & PAMD_FLAG_ONE_CHAIN_PER_LAUNCH) != 0;
-    if (!P->h_ho.empty()) {
-        if (!one) {
-            PAMD_CUDA_TRY(launch_ho_action<R>(P->d_ho, (int)P->h_ho.size(), P->max_s_ho, pos, grad,
-                                              P->d_part_S, 0, a, ginv, with_grad, st));
-        } else {
-            for (int c = 0; c < P->n_chains; ++c) {
-                const int f = P->ho_chain_first[c];
-                if (f < 0) continue;
-                PAMD_CUDA_TRY(launch_ho_action<R>(P->d_ho + f, P->ho_chain_count[c], P->max_s_ho, pos,
-                                                  grad, P->d_part_S, f, a, ginv, with_grad, st));
-            }
+    // harmonic systems: one launch per system (per chain in the plain form)
+    for (const auto& si : P->sys) {
+        if (si.kind != PAMD_HARMONIC) continue;
+        const int sz = si.d * si.N;
+        const long long lo = si.off, hi = si.off + si.chain_len * si.chains;
+        for (int c = one ? 0 : -1; c < (one ? si.chains : 0); ++c) {
+            const int b0 = one ? P->ho_chain_first[si.chain0 + c] : si.ho_b0;
+            const int nb = one ? P->ho_chain_count[si.chain0 + c] : si.ho_b1 - si.ho_b0;
+            if (std::is_same<R, float>::value && sz <= 4)
+                PAMD_CUDA_TRY(launch_ho_action_vec(P->d_ho + b0, nb, sz, (const float*)pos,
+                                                   (float*)grad, P->d_part_S, b0, a, ginv, with_grad,
+                                                   lo, hi, st));
+            else
+                PAMD_CUDA_TRY(launch_ho_action<R>(P->d_ho + b0, nb, P->max_s_ho, pos, grad, P->d_part_S,
+                                                  b0, a, ginv, with_grad, st));
         }
     }
     if (P->n_lj_items > 0) {
@@ -494,7 +505,7 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
         }
     }
     PAMD_CUDA_TRY(launch_finalize(P->d_part_S, P->d_S_slots, P->n_chains, 1.0 / (4.0 * p->D * p->dt),
-                                  S_out, st));
+                                  S_out, st, P->d_err));
     return PAMD_OK;
 }
 
@@ -545,6 +556,23 @@ int pamd_release_cache(void)
     cudaDeviceSynchronize();
     g_plans.clear();
     return PAMD_OK;
+}
+
+int pamd_device_status(void* stream)
+{
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PAMD_ERR_CUDA;
+    int worst = PAMD_OK;
+    for (auto& kv : g_plans) {
+        int v = 0;
+        if (cudaMemcpy(&v, kv.second->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return PAMD_ERR_CUDA;
+        if (v != PAMD_OK) {
+            worst = v;
+            cudaMemset(kv.second->d_err, 0, sizeof(int));
+        }
+    }
+    return worst;
 }
 
 int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin)

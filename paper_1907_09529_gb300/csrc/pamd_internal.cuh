@@ -160,6 +160,13 @@ cudaError_t launch_ho_action(const ElemBlock* blocks, int n_blocks, int max_s, c
                              double* partials, int slot0, double a, double ginv, bool with_grad,
                              cudaStream_t st);
 
+// Single-precision form for slices of s <= 4 elements: aligned float4 loads and
+// stores, neighbours from registers.  The blocks must all belong to one system
+// whose elements span [sys_lo, sys_hi) of the buffer (reads stay inside it).
+cudaError_t launch_ho_action_vec(const ElemBlock* blocks, int n_blocks, int s, const float* pos,
+                                 float* grad, double* partials, int slot0, double a, double ginv,
+                                 bool with_grad, long long sys_lo, long long sys_hi, cudaStream_t st);
+
 struct LJConst {
     double L, rc, eps, sigma, a, ginv, skin;
 };
@@ -248,9 +255,10 @@ cudaError_t launch_lj_euler(R* pos, const R* noise, const void* sys_entry_host, 
                             int n_chains, int chain0, uint64_t seed, uint64_t counter,
                             cudaStream_t st);
 
-// Deterministic per-chain sums of partials: out[c] = scale * sum(partials[slots[c]]).
+// Deterministic per-chain sums of partials: out[c] = scale * sum(partials[slots[c]]);
+// a non-finite sum sets *err (if given) to PAMD_ERR_NONFINITE.
 cudaError_t launch_finalize(const double* partials, const ChainSlots* slots, int n_chains,
-                            double scale, double* out, cudaStream_t st);
+                            double scale, double* out, cudaStream_t st, int* err = nullptr);
 
 // MALA update pieces (element-wise over all systems' blocks).
 struct MalaDev {

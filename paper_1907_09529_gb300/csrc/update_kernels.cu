@@ -17,7 +17,8 @@ namespace pamd {
 // One warp per chain: fixed lane assignment and a fixed shuffle tree, so the
 // result is bitwise reproducible.
 __global__ void finalize_kernel(const double* __restrict__ partials, const ChainSlots* __restrict__ slots,
-                                int n_chains, double scale, double* __restrict__ out)
+                                int n_chains, double scale, double* __restrict__ out,
+                                int* __restrict__ err)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -26,16 +27,19 @@ __global__ void finalize_kernel(const double* __restrict__ partials, const Chain
     double s = 0.0;
     for (int q = cs.begin + lane; q < cs.end; q += 32) s += partials[q];
     s = warp_sum(s);
-    if (lane == 0) out[warp] = s * scale;
+    if (lane == 0) {
+        out[warp] = s * scale;
+        if (err && !isfinite(s)) atomicExch(err, PAMD_ERR_NONFINITE);
+    }
 }
 
 cudaError_t launch_finalize(const double* partials, const ChainSlots* slots, int n_chains,
-                            double scale, double* out, cudaStream_t st)
+                            double scale, double* out, cudaStream_t st, int* err)
 {
     if (n_chains <= 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (n_chains * 32 + threads - 1) / threads;
-    finalize_kernel<<<blocks, threads, 0, st>>>(partials, slots, n_chains, scale, out);
+    finalize_kernel<<<blocks, threads, 0, st>>>(partials, slots, n_chains, scale, out, err);
     return cudaGetLastError();
 }
 

@@ -352,3 +352,19 @@ def test_invalid_arguments_are_rejected(pamd):
     S = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(pamd.PamdError):
         pamd.path_update(prob, buf, buf.clone(), S, h=-1.0)
+
+
+def test_nonfinite_action_is_reported(pamd):
+    """Two particles on top of each other give an infinite action; the library
+    flags it on the device and pamd_device_status reports it once."""
+    prob = pamd.Problem([pamd.System("lj", 4, 3, 3, 1, box=6.0, rc=2.5)], 1.0, 1.0, 1e-4)
+    buf = prob.empty("cuda")
+    v = prob.view(buf, 0)
+    v[0, :, :, :] = torch.tensor([[0.5, 2.0, 3.5, 5.0]] * 3, device="cuda")
+    v[0, :, :, 1] = v[0, :, :, 0]  # particles 0 and 1 coincide at every slice
+    pamd.device_status()  # clear anything earlier
+    S, g = pamd.action_grad(prob, buf)
+    with pytest.raises(pamd.PamdError) as ei:
+        pamd.device_status()
+    assert ei.value.status == -5
+    pamd.device_status()  # cleared
