@@ -367,8 +367,8 @@ def main():
         peak = float(peaks.get("hbm_gbs", 6800.0))
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": profiled_traffic(args.config, "ho_action_kernel"),
-                "kernel": "ho_action_kernel<float,true>", "peak_note":
+                "traffic": profiled_traffic(args.config, "ho_vec_kernel"),
+                "kernel": "ho_vec_kernel<s,true>", "peak_note":
                 "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
                 "bytes_per_launch": nbytes, "kernel_ms": ms_kernel}
 
