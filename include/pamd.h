@@ -158,6 +158,36 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
 int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uint64_t counter,
                          const void* noise, void* stream);
 
+/* n_steps multilevel sliding-and-sampling Monte Carlo steps (paper Sec. III,
+ * Fig. 5) of every chain of harmonic systems, with free-particle trial paths.
+ * A step of a chain draws a level l in [l_min, l_max] and an offset o in
+ * [0, 2^l); the fragments' shared endpoints are 0 and o + k 2^l (0 < . < T),
+ * the tail x_0 and the shared endpoints stay fixed and the nose fragment moves
+ * x_T.  Each fragment is accepted or rejected on its own by Metropolis-Hastings
+ * with a Brownian-bridge trial (random walk for the nose):
+ *     log alpha = -(S(X') - S(X)) + (S0(X') - S0(X)),  S0 = free-particle action,
+ * both over the fragment's steps, in double precision.
+ *   pos         : in/out, device buffer (precision's element type).
+ *   l_min,l_max : 1 <= l_min <= l_max, 2^l_max <= T of every system.
+ *   seed,counter: Philox key and counter (step u uses counter+u; streams 3-5:
+ *                 level/offset from words 0/1 modulo the range, trial normals,
+ *                 per-fragment 53-bit uniforms).
+ *   levels, offsets : NULL, or (only with n_steps == 1) int[n_chains_total]
+ *                 each, the fragmentation of every chain.
+ *   noise       : NULL, or (n_steps == 1) standard normals in the layout of pos;
+ *                 slice t+1's entries drive the trial step t -> t+1.
+ *   log_u       : NULL, or (n_steps == 1) double[n_chains_total * F] with
+ *                 F = max over systems of (T >> l_min) + 2; fragment f (counted
+ *                 from the tail) of chain c uses log_u[c*F + f].
+ *   n_accepted, n_proposed : int[n_chains_total], incremented (fragments with
+ *                 interior points are proposed).
+ * Device pointers only (host pointers: PAMD_ERR_ARG); Lennard-Jones systems:
+ * PAMD_ERR_UNSUPPORTED (their trial needs a hard-sphere pair propagator). */
+int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, int n_steps,
+                     uint64_t seed, uint64_t counter, const int* levels, const int* offsets,
+                     const void* noise, const double* log_u, int* n_accepted, int* n_proposed,
+                     void* stream);
+
 /* Diagnostics for bit-exact index parity: number of ordered in-cutoff pairs
  * (i != j) of every slice of every LJ chain, decided in single precision by
  * the kernels' rule (dx = xi - xj; k = fmaf(dx, 1/L, 1.5*2^23) - 1.5*2^23;

@@ -100,6 +100,8 @@ def _load():
             "or_mala_step": (c_int, [_P, c_int, c_int, c_int, c_double, c_double, c_double, c_double,
                                      _D, c_double, _D, _D, c_double, c_int, _D, _D, _D, _D, _I,
                                      c_int]),
+            "or_fragment_step": (c_int, [_P, c_int, c_int, c_int, c_double, c_double, c_double,
+                                         c_int, c_int, _D, _D, _D, _I, _I]),
             "or_philox4x32_10": (None, [_U32, _U32, _U32]),
             "or_normals": (None, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                   ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, _D]),
@@ -263,6 +265,30 @@ def mala_step(pot: Potential, pos: np.ndarray, S: float, grad: np.ndarray, eta: 
         raise MemoryError("oracle mala_step")
     return dict(prop=prop, S_prop=Sp.value, grad_prop=gp, log_alpha=la.value,
                 accepted=bool(acc.value))
+
+
+def fragment_step(pot: Potential, pos: np.ndarray, level: int, offset: int, z: np.ndarray,
+                  log_u, D: float, beta: float, dt: float):
+    """One multilevel sliding-and-sampling MC step (Sec. III, Fig. 5) with
+    free-particle trials; pos [T+1][d][N] is updated in place.  z has the layout
+    of pos (slice-0 entries unused); log_u holds one log uniform per fragment.
+    Returns (n_fragments, n_accepted, n_proposed)."""
+    assert pos.dtype == np.float64 and pos.flags.c_contiguous
+    T = pos.shape[0] - 1
+    _, d, N = pos.shape
+    z = _f64(z)
+    lu = _f64(log_u)
+    acc, prop = ctypes.c_int(0), ctypes.c_int(0)
+    nf = _load().or_fragment_step(ctypes.byref(pot), N, d, T, D, beta, dt, int(level), int(offset),
+                                  _d(z), _d(lu), _d(pos), ctypes.byref(acc), ctypes.byref(prop))
+    if nf < 0:
+        raise MemoryError("oracle fragment_step")
+    return nf, acc.value, prop.value
+
+
+def n_fragments(T: int, level: int, offset: int) -> int:
+    """Fragments of a path of T steps at this level and offset."""
+    return 1 + sum(1 for e in range(offset, T, 1 << level) if e > 0)
 
 
 # ---------------------------------------------------------------- random numbers

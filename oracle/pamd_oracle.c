@@ -420,6 +420,95 @@ int or_mala_step(const or_potential* p, int N, int d, int T, double D, double be
 }
 
 /* ---------------------------------------------------------------- */
+/* One multilevel sliding-and-sampling Monte Carlo step (paper Sec. III,
+ * Fig. 5) at level `level` with fragmentation offset `offset` in [0, 2^level).
+ * Shared fragment endpoints sit at 0 and at offset + k 2^level (0 < . < T); the
+ * tail x_0 and every shared endpoint stay fixed, the nose fragment
+ * [last endpoint, T] moves its end x_T.  Each fragment is updated
+ * independently by Metropolis-Hastings with a trial path of the free particle
+ * (V = 0) with the same D and dt: a Brownian bridge between the fixed ends of
+ * an interior fragment, a free random walk for the nose.  The trial density is
+ * exp(-S0) with S0 = sum |x_{t+1} - x_t|^2 / (4 D dt) (up to factors that do not
+ * depend on the interior points), so
+ *     log alpha = -(S(X') - S(X)) + (S0(X') - S0(X)),
+ * both differences over the fragment's own steps.  Trial construction, step by
+ * step with z[t+1][m] standard normals and sig = sqrt(2 D dt):
+ *     bridge:  x'_{t+1} = x'_t + (x_b - x'_t)/(b - t) + sig sqrt((b-t-1)/(b-t)) z_{t+1}
+ *     nose:    x'_{t+1} = x'_t + sig z_{t+1}.
+ * log_u[f] decides fragment f (in order from the tail).  Returns the number of
+ * fragments; *n_acc counts accepted fragments with interior points. */
+int or_fragment_step(const or_potential* p, int N, int d, int T, double D, double beta, double dt,
+                     int level, int offset, const double* z, const double* log_u, double* pos,
+                     int* n_acc, int* n_prop)
+{
+    int M = d * N;
+    double a = beta * D * dt, sig = sqrt(2.0 * D * dt), c4 = 1.0 / (4.0 * D * dt);
+    int len = 1 << level;
+    double* trial = (double*)malloc(sizeof(double) * (size_t)(T + 1) * M);
+    double* F = (double*)malloc(sizeof(double) * (size_t)M);
+    double* Ft = (double*)malloc(sizeof(double) * (size_t)M);
+    if (!trial || !F || !Ft) { free(trial); free(F); free(Ft); return -1; }
+    /* fragment boundaries */
+    int nb = 0;
+    int* bnd = (int*)malloc(sizeof(int) * (size_t)(T / len + 3));
+    bnd[nb++] = 0;
+    for (int e = offset; e < T; e += len)
+        if (e > 0) bnd[nb++] = e;
+    bnd[nb++] = T;
+    int nfrag = nb - 1;
+    *n_acc = 0;
+    *n_prop = 0;
+    for (int f = 0; f < nfrag; ++f) {
+        int fa = bnd[f], fb = bnd[f + 1];
+        int nose = (f == nfrag - 1);
+        if (!nose && fb - fa < 2) continue; /* no interior point */
+        ++*n_prop;
+        /* trial path on [fa, fb] */
+        for (int m = 0; m < M; ++m) trial[(size_t)fa * M + m] = pos[(size_t)fa * M + m];
+        for (int t = fa; t < fb; ++t)
+            for (int m = 0; m < M; ++m) {
+                double xt = trial[(size_t)t * M + m];
+                double zz = z[(size_t)(t + 1) * M + m];
+                double y;
+                if (nose) {
+                    y = xt + sig * zz;
+                } else if (t + 1 == fb) {
+                    y = pos[(size_t)fb * M + m];
+                } else {
+                    double xb = pos[(size_t)fb * M + m];
+                    double rem = (double)(fb - t);
+                    y = xt + (xb - xt) / rem + sig * sqrt((rem - 1.0) / rem) * zz;
+                }
+                trial[(size_t)(t + 1) * M + m] = y;
+            }
+        /* action differences over the fragment's steps */
+        double dS = 0.0, dS0 = 0.0;
+        for (int t = fa; t < fb; ++t) {
+            or_force(p, N, d, pos + (size_t)t * M, F);
+            or_force(p, N, d, trial + (size_t)t * M, Ft);
+            for (int m = 0; m < M; ++m) {
+                double x0 = pos[(size_t)t * M + m], x1 = pos[(size_t)(t + 1) * M + m];
+                double y0 = trial[(size_t)t * M + m], y1 = trial[(size_t)(t + 1) * M + m];
+                double r = x1 - x0 - a * F[m], rt = y1 - y0 - a * Ft[m];
+                dS += (rt * rt - r * r) * c4;
+                dS0 += ((y1 - y0) * (y1 - y0) - (x1 - x0) * (x1 - x0)) * c4;
+            }
+        }
+        double la = -dS + dS0;
+        if (log_u[f] < la) {
+            ++*n_acc;
+            for (int t = fa + 1; t <= fb; ++t)
+                for (int m = 0; m < M; ++m) pos[(size_t)t * M + m] = trial[(size_t)t * M + m];
+        }
+    }
+    free(bnd);
+    free(trial);
+    free(F);
+    free(Ft);
+    return nfrag;
+}
+
+/* ---------------------------------------------------------------- */
 /* Philox4x32-10 counter-based generator, written from its published
  * definition (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
  * easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with

@@ -18,6 +18,7 @@ import torch
 from . import _lib
 from ._lib import (PAMD_FLAG_ONE_CHAIN_PER_LAUNCH, PAMD_FP32, PAMD_FP64, PAMD_HARMONIC, PAMD_LJ,
                    PamdError, pamd_action, pamd_action_grad, pamd_device_status, pamd_euler_reference,
+                   pamd_fragment_mc,
                    pamd_lj_pair_counts, pamd_normals, pamd_path_update, pamd_philox,
                    pamd_release_cache, pamd_tune, pamd_version)
 
@@ -26,7 +27,8 @@ __all__ = [
     "lj_pair_counts", "philox", "normals", "PamdAction", "PamdError", "tune", "release_cache",
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_release_cache", "pamd_tune",
-    "pamd_version", "pamd_device_status", "device_status",
+    "pamd_version", "pamd_device_status", "device_status", "pamd_fragment_mc", "fragment_mc",
+    "fragment_slots",
 ]
 
 ALIGN = 8  # system offsets are rounded to 8 elements (>= 16 bytes)
@@ -159,6 +161,28 @@ def euler_reference(p: Problem, pos: torch.Tensor, seed: int = 0, counter: int =
     pamd_euler_reference(p.ref, _ptr(pos), int(seed), int(counter), _ptr(noise),
                          _stream(pos, stream))
     return pos
+
+
+def fragment_slots(p: Problem, l_min: int) -> int:
+    """Per-chain stride of the log_u array of fragment_mc."""
+    return max(s.T for s in p.systems) // (1 << l_min) + 2
+
+
+def fragment_mc(p: Problem, pos: torch.Tensor, l_min: int, l_max: int, n_steps: int = 1,
+                seed: int = 0, counter: int = 0, levels: Optional[torch.Tensor] = None,
+                offsets: Optional[torch.Tensor] = None, noise: Optional[torch.Tensor] = None,
+                log_u: Optional[torch.Tensor] = None, n_accepted: Optional[torch.Tensor] = None,
+                n_proposed: Optional[torch.Tensor] = None, stream=None):
+    """Multilevel sliding-and-sampling MC steps (Sec. III) of harmonic paths."""
+    _check_buf(p, pos, "pos")
+    if n_accepted is None:
+        n_accepted = torch.zeros(p.n_chains, dtype=torch.int32, device=pos.device)
+    if n_proposed is None:
+        n_proposed = torch.zeros(p.n_chains, dtype=torch.int32, device=pos.device)
+    pamd_fragment_mc(p.ref, _ptr(pos), int(l_min), int(l_max), int(n_steps), int(seed),
+                     int(counter), _ptr(levels), _ptr(offsets), _ptr(noise), _ptr(log_u),
+                     _ptr(n_accepted), _ptr(n_proposed), _stream(pos, stream))
+    return n_accepted, n_proposed
 
 
 def lj_pair_counts(p: Problem, pos: torch.Tensor, stream=None) -> torch.Tensor:

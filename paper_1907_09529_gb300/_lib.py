@@ -32,7 +32,7 @@ EXPORTS = (
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
-    "pamd_device_status",
+    "pamd_device_status", "pamd_fragment_mc",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
                                          ctypes.c_double]),
             "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
             "pamd_device_status": (ctypes.c_int, [_VP]),
+            "pamd_fragment_mc": (ctypes.c_int, [_PP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                u64, u64, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -151,6 +153,12 @@ def pamd_normals(seed, counter, stream_id, chain, e0, n, out, stream):
 
 def pamd_tune(tile_steps, threads_per_particle, max_neighbours, skin):
     return _call("pamd_tune", tile_steps, threads_per_particle, max_neighbours, skin)
+
+
+def pamd_fragment_mc(prob, pos, l_min, l_max, n_steps, seed, counter, levels, offsets, noise,
+                     log_u, n_accepted, n_proposed, stream):
+    return _call("pamd_fragment_mc", prob, pos, l_min, l_max, n_steps, seed, counter, levels,
+                 offsets, noise, log_u, n_accepted, n_proposed, stream)
 
 
 def pamd_device_status(stream):

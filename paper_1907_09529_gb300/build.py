@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpamd.so")
-SOURCES = ["pamd_api.cu", "ho_kernels.cu", "lj_kernels.cu", "update_kernels.cu", "noalloc.cu"]
+SOURCES = ["pamd_api.cu", "ho_kernels.cu", "lj_kernels.cu", "update_kernels.cu", "noalloc.cu",
+           "fragment_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
@@ -58,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -15,11 +15,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pamd_internal.cuh"
 
 using namespace pamd;
 
 namespace {
+
+// NVTX range around every entry point (visible in Nsight tools; a no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define PAMD_CUDA_TRY(expr)                           \
     do {                                              \
@@ -592,6 +600,7 @@ int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, doub
 static int action_common(const pamd_problem* prob, const void* pos, double* S, void* grad,
                          bool with_grad, void* stream)
 {
+    NvtxRange nvtx_(with_grad ? "pamd_action_grad" : "pamd_action");
     int rc = check_problem(prob);
     if (rc) return rc;
     if (!pos || !S || (with_grad && !grad)) return PAMD_ERR_ARG;
@@ -644,6 +653,7 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
                      int n_updates, uint64_t seed, uint64_t counter, const void* noise,
                      const double* log_u, int* n_accepted, double* log_alpha, void* stream)
 {
+    NvtxRange nvtx_("pamd_path_update");
     int rc = check_problem(prob);
     if (rc) return rc;
     if (!pos || !grad || !S || !(h > 0) || n_updates < 0) return PAMD_ERR_ARG;
@@ -757,6 +767,7 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
 int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uint64_t counter,
                          const void* noise, void* stream)
 {
+    NvtxRange nvtx_("pamd_euler_reference");
     int rc = check_problem(prob);
     if (rc) return rc;
     if (!pos) return PAMD_ERR_ARG;
@@ -811,8 +822,58 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
     return PAMD_OK;
 }
 
+int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, int n_steps,
+                     uint64_t seed, uint64_t counter, const int* levels, const int* offsets,
+                     const void* noise, const double* log_u, int* n_accepted, int* n_proposed,
+                     void* stream)
+{
+    NvtxRange nvtx_("pamd_fragment_mc");
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!pos || !n_accepted || !n_proposed || n_steps < 0 || l_min < 1 || l_max < l_min || l_max > 30)
+        return PAMD_ERR_ARG;
+    if ((levels || offsets || noise || log_u) && n_steps != 1) return PAMD_ERR_ARG;
+    if ((levels == nullptr) != (offsets == nullptr)) return PAMD_ERR_ARG;
+    int Tmax = 0;
+    for (int q = 0; q < prob->n_systems; ++q) {
+        const pamd_system& s = prob->systems[q];
+        if (s.pot.kind != PAMD_HARMONIC) return PAMD_ERR_UNSUPPORTED;
+        if ((1LL << l_max) > s.n_steps) return PAMD_ERR_ARG;
+        Tmax = std::max(Tmax, s.n_steps);
+    }
+    for (const void* ptr : {(const void*)pos, (const void*)levels, (const void*)offsets, noise,
+                            (const void*)log_u, (const void*)n_accepted, (const void*)n_proposed})
+        if (ptr && is_host_ptr(ptr)) return PAMD_ERR_ARG;  // device buffers only
+    const int fstride = (Tmax >> l_min) + 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double a = prob->beta * prob->D * prob->dt, sig = std::sqrt(2.0 * prob->D * prob->dt);
+    const double c4 = 1.0 / (4.0 * prob->D * prob->dt);
+    for (int u = 0; u < n_steps; ++u) {
+        int chain0 = 0;
+        for (int q = 0; q < prob->n_systems; ++q) {
+            const pamd_system& s = prob->systems[q];
+            const int M = s.dim * s.n_particles;
+            if (prob->precision == PAMD_FP64)
+                PAMD_CUDA_TRY(launch_fragment_mc<double>((double*)pos, s.pos_offset, s.n_steps, M,
+                                                         s.n_chains, chain0, s.pot.k, l_min, l_max,
+                                                         seed, counter + u, levels, offsets,
+                                                         (const double*)noise, log_u, fstride, a,
+                                                         sig, c4, n_accepted, n_proposed, st));
+            else
+                PAMD_CUDA_TRY(launch_fragment_mc<float>((float*)pos, s.pos_offset, s.n_steps, M,
+                                                        s.n_chains, chain0, s.pot.k, l_min, l_max,
+                                                        seed, counter + u, levels, offsets,
+                                                        (const float*)noise, log_u, fstride, a, sig,
+                                                        c4, n_accepted, n_proposed, st));
+            chain0 += s.n_chains;
+        }
+    }
+    return PAMD_OK;
+}
+
 int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* counts, void* stream)
 {
+    NvtxRange nvtx_("pamd_lj_pair_counts");
     int rc = check_problem(prob);
     if (rc) return rc;
     if (!pos || !counts || prob->precision != PAMD_FP32) return PAMD_ERR_ARG;

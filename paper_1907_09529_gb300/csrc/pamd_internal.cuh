@@ -104,7 +104,14 @@ __device__ __forceinline__ double philox_uniform53(uint64_t seed, uint64_t count
     return ((double)m + 1.0) * 1.1102230246251565e-16;  // 2^-53
 }
 
-enum : uint32_t { kStreamEuler = 0, kStreamMala = 1, kStreamAccept = 2 };
+enum : uint32_t {
+    kStreamEuler = 0,
+    kStreamMala = 1,
+    kStreamAccept = 2,
+    kStreamFragCut = 3,
+    kStreamFragTrial = 4,
+    kStreamFragAccept = 5
+};
 
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v)
@@ -286,6 +293,15 @@ cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter,
                                    cudaStream_t st);
 
 cudaError_t launch_philox(uint4 ctr, uint2 key, long long n, uint32_t* out, cudaStream_t st);
+
+// One multilevel sliding-and-sampling MC step of every chain of one harmonic
+// system (free-particle trials).
+template <typename R>
+cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains, int chain0,
+                               double k, int l_min, int l_max, uint64_t seed, uint64_t counter,
+                               const int* levels, const int* offsets, const R* noise,
+                               const double* log_u, int fstride, double a, double sig, double c4,
+                               int* n_accepted, int* n_proposed, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain,
                            long long e0, long long n, float* out, cudaStream_t st);
 

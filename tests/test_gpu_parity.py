@@ -370,3 +370,34 @@ def test_nonfinite_action_is_reported(pamd):
         pamd.device_status()
     assert ei.value.status == -5
     pamd.device_status()  # cleared
+
+
+def test_checkpoint_resume_is_bitwise_identical(pamd, tmp_path):
+    """20 updates in one run == 10 updates, checkpoint, reload, 10 more updates."""
+    from paper_1907_09529_gb300 import checkpoint
+    w = inputs.workload("lj108", "small")
+    paths = start_paths(w, "fp32")
+    prob = _problem(pamd, w, "fp32")
+
+    def fresh():
+        buf = _upload(pamd, prob, paths)
+        S, g = pamd.action_grad(prob, buf)
+        return checkpoint.RunState(buf, g, S, torch.zeros(prob.n_chains, dtype=torch.int32,
+                                                         device="cuda"), seed=5, counter=1000)
+
+    a = fresh()
+    pamd.path_update(prob, a.pos, a.grad, a.S, 1e-6, n_updates=20, seed=a.seed, counter=a.counter,
+                     n_accepted=a.n_accepted)
+    b = fresh()
+    pamd.path_update(prob, b.pos, b.grad, b.S, 1e-6, n_updates=10, seed=b.seed, counter=b.counter,
+                     n_accepted=b.n_accepted)
+    b.counter += 10
+    f = str(tmp_path / "run.pt")
+    checkpoint.save(f, prob, b)
+    c = checkpoint.load(f, prob)
+    pamd.path_update(prob, c.pos, c.grad, c.S, 1e-6, n_updates=10, seed=c.seed, counter=c.counter,
+                     n_accepted=c.n_accepted)
+    torch.cuda.synchronize()
+    assert torch.equal(prob.view(a.pos, 0), prob.view(c.pos, 0))
+    assert torch.equal(a.S, c.S) and torch.equal(a.n_accepted, c.n_accepted)
+    assert torch.equal(prob.view(a.grad, 0), prob.view(c.grad, 0))

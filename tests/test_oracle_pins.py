@@ -412,3 +412,62 @@ def test_pair_count_f32_agrees_with_exact_distances():
         if np.abs(r - rc).min() < 1e-4:
             continue
         assert oracle.pair_count_f32(L, rc, x32) == int((r <= rc).sum())
+
+
+# ---------------------------------------------------------------- multilevel sliding-and-sampling MC
+@pytest.mark.slow
+@pytest.mark.parametrize("levels", [(1, 1), (2, 3)])
+def test_fragment_mc_samples_the_path_distribution(levels):
+    """Repeated multilevel fragment MC steps (free-particle trials) leave the
+    oscillator path distribution exp(-S) with x_0 fixed invariant: sampled x_4
+    and x_8 match the exact AR(1) marginals of the Euler-Maruyama chain."""
+    T, dt, x0v = 8, 0.1, 1.0
+    p = oracle.harmonic(1.0)
+    a = 1 - dt
+    pos = np.zeros((T + 1, 1, 1))
+    pos[0] = x0v
+    g = inputs.rng(91 + levels[0])
+    n_steps, burn = 30000, 500
+    samples = []
+    acc = prop = 0
+    for it in range(n_steps):
+        l = int(g.integers(levels[0], levels[1] + 1))
+        o = int(g.integers(0, 1 << l))
+        z = g.standard_normal(pos.shape)
+        nf = oracle.n_fragments(T, l, o)
+        lu = np.log(g.random(nf))
+        nf2, na, npr = oracle.fragment_step(p, pos, l, o, z, lu, 1.0, 1.0, dt)
+        assert nf2 == nf
+        acc += na
+        prop += npr
+        if it >= burn:
+            samples.append(pos[[4, 8], 0, 0].copy())
+    assert np.all(pos[0] == x0v)
+    assert 0.2 < acc / prop < 1.0
+    samples = np.array(samples)
+    for col, t in enumerate((4, 8)):
+        m = a ** t * x0v
+        v = 2 * dt * (1 - a ** (2 * t)) / (1 - a ** 2)
+        xs = samples[:, col]
+        nb = 50
+        k = len(xs) // nb * nb
+        bm = xs[:k].reshape(nb, -1).mean(1)
+        bv = ((xs[:k] - m) ** 2).reshape(nb, -1).mean(1)
+        assert abs(bm.mean() - m) < 5 * bm.std(ddof=1) / math.sqrt(nb)
+        assert abs(bv.mean() - v) < 5 * bv.std(ddof=1) / math.sqrt(nb)
+
+
+def test_fragment_layout_and_fixed_endpoints():
+    """Endpoints shared by fragments (and the tail) never move; the nose does."""
+    T = 16
+    p = oracle.harmonic(1.0)
+    pos = inputs.normals(5, (T + 1, 1, 1))
+    before = pos.copy()
+    z = inputs.normals(6, pos.shape)
+    lu = np.full(oracle.n_fragments(T, 2, 1), -np.inf)  # accept everything
+    nf, na, npr = oracle.fragment_step(p, pos, 2, 1, z, lu, 1.0, 1.0, 0.1)
+    assert nf == 5  # [0,1] [1,5] [5,9] [9,13] [13,16]
+    for e in (0, 1, 5, 9, 13):
+        assert pos[e, 0, 0] == before[e, 0, 0]
+    assert pos[16, 0, 0] != before[16, 0, 0]
+    assert na == npr == 4  # [0,1] has no interior point
