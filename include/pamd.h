@@ -188,6 +188,22 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
                      const void* noise, const double* log_u, int* n_accepted, int* n_proposed,
                      void* stream);
 
+/* Shift and regenerate (paper Fig. 2): every chain's trajectory advances by
+ * n_shift steps and its path is grown back to n_steps at the nose.
+ *   pos     : path buffer, read (device).
+ *   pos_out : another path buffer of the same layout, written: slices
+ *             0..T-n_shift are pos's slices n_shift..T; the last n_shift slices
+ *             continue from the nose by free-particle steps x + sqrt(2 D dt) z
+ *             (the sampler's trial distribution).
+ *   traj    : written, the trajectory points x_1..x_{n_shift} of every chain:
+ *             [chains][n_shift][dim][N] per system, systems one after another.
+ *   noise   : NULL (Philox stream 6, seed/counter) or standard normals
+ *             [n_chains_total][n_shift][dim][N] (every system uses its dim*N).
+ * Device pointers only; pos and pos_out must differ. */
+int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_out, int n_shift,
+                          void* traj, uint64_t seed, uint64_t counter, const void* noise,
+                          void* stream);
+
 /* Diagnostics for bit-exact index parity: number of ordered in-cutoff pairs
  * (i != j) of every slice of every LJ chain, decided in single precision by
  * the kernels' rule (dx = xi - xj; k = fmaf(dx, 1/L, 1.5*2^23) - 1.5*2^23;

@@ -102,6 +102,8 @@ def _load():
                                      c_int]),
             "or_fragment_step": (c_int, [_P, c_int, c_int, c_int, c_double, c_double, c_double,
                                          c_int, c_int, _D, _D, _D, _I, _I]),
+            "or_shift_regenerate": (None, [c_int, c_int, c_int, c_double, c_double, c_int, _D, _D,
+                                           _D, _D]),
             "or_philox4x32_10": (None, [_U32, _U32, _U32]),
             "or_normals": (None, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                   ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, _D]),
@@ -284,6 +286,18 @@ def fragment_step(pot: Potential, pos: np.ndarray, level: int, offset: int, z: n
     if nf < 0:
         raise MemoryError("oracle fragment_step")
     return nf, acc.value, prop.value
+
+
+def shift_regenerate(pos: np.ndarray, n_shift: int, z: np.ndarray, D: float, dt: float):
+    """Shift by n_shift steps and regrow the nose with free-particle steps (Fig. 2).
+    Returns (new path, trajectory points x_1..x_{n_shift})."""
+    pos, z = _f64(pos), _f64(z)
+    T = pos.shape[0] - 1
+    _, d, N = pos.shape
+    out = np.empty_like(pos)
+    traj = np.empty((n_shift, d, N))
+    _load().or_shift_regenerate(N, d, T, D, dt, int(n_shift), _d(pos), _d(z), _d(out), _d(traj))
+    return out, traj
 
 
 def n_fragments(T: int, level: int, offset: int) -> int:

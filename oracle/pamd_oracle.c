@@ -509,6 +509,29 @@ int or_fragment_step(const or_potential* p, int N, int d, int T, double D, doubl
 }
 
 /* ---------------------------------------------------------------- */
+/* Shift and regenerate (paper Fig. 2, Sec. II.A): the trajectory advances by
+ * n_shift steps -- traj[k] = x_{k+1}, k < n_shift -- the path drops its first
+ * n_shift steps, and n_shift new slices are grown from the nose with the
+ * trial distribution of the sampler (free particle):
+ *     out[t] = pos[t + n_shift]                      (t <= T - n_shift)
+ *     out[T - n_shift + k] = out[T - n_shift + k - 1] + sqrt(2 D dt) z[k-1]   (k = 1..n_shift)
+ * z is [n_shift][M] standard normals. */
+void or_shift_regenerate(int N, int d, int T, double D, double dt, int n_shift, const double* pos,
+                         const double* z, double* out, double* traj)
+{
+    int M = d * N;
+    double sig = sqrt(2.0 * D * dt);
+    for (int k = 0; k < n_shift; ++k)
+        for (int m = 0; m < M; ++m) traj[(size_t)k * M + m] = pos[(size_t)(k + 1) * M + m];
+    for (int t = 0; t <= T - n_shift; ++t)
+        for (int m = 0; m < M; ++m) out[(size_t)t * M + m] = pos[(size_t)(t + n_shift) * M + m];
+    for (int k = 1; k <= n_shift; ++k)
+        for (int m = 0; m < M; ++m)
+            out[(size_t)(T - n_shift + k) * M + m] =
+                out[(size_t)(T - n_shift + k - 1) * M + m] + sig * z[(size_t)(k - 1) * M + m];
+}
+
+/* ---------------------------------------------------------------- */
 /* Philox4x32-10 counter-based generator, written from its published
  * definition (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
  * easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with

@@ -32,7 +32,7 @@ EXPORTS = (
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
-    "pamd_device_status", "pamd_fragment_mc",
+    "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
             "pamd_device_status": (ctypes.c_int, [_VP]),
             "pamd_fragment_mc": (ctypes.c_int, [_PP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 u64, u64, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+            "pamd_shift_regenerate": (ctypes.c_int, [_PP, _VP, _VP, ctypes.c_int, _VP, u64, u64,
+                                                     _VP, _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -159,6 +161,11 @@ def pamd_fragment_mc(prob, pos, l_min, l_max, n_steps, seed, counter, levels, of
                      log_u, n_accepted, n_proposed, stream):
     return _call("pamd_fragment_mc", prob, pos, l_min, l_max, n_steps, seed, counter, levels,
                  offsets, noise, log_u, n_accepted, n_proposed, stream)
+
+
+def pamd_shift_regenerate(prob, pos, pos_out, n_shift, traj, seed, counter, noise, stream):
+    return _call("pamd_shift_regenerate", prob, pos, pos_out, n_shift, traj, seed, counter, noise,
+                 stream)
 
 
 def pamd_device_status(stream):

@@ -17,6 +17,8 @@
 // action differences in double, draws its own uniform, and on acceptance builds
 // the same trial again (same normals) and writes it.  Fragments share only
 // fixed endpoints, so the writes never overlap.
+#include <algorithm>
+
 #include "pamd_internal.cuh"
 
 namespace pamd {
@@ -166,5 +168,79 @@ template cudaError_t launch_fragment_mc<double>(double*, long long, int, int, in
                                                 int, uint64_t, uint64_t, const int*, const int*,
                                                 const double*, const double*, int, double, double,
                                                 double, int*, int*, cudaStream_t);
+
+// ------------------------------------------------------------------ shift and regenerate
+// Trajectory points x_1..x_{n_shift} of every chain are copied out, the path is
+// shifted by n_shift steps into `out`, and the last n_shift slices of `out` are
+// grown from the nose by free-particle steps x + sqrt(2 D dt) z (paper Fig. 2:
+// the regenerated slices come from the sampler's trial distribution).
+template <typename R>
+__global__ void shift_copy_kernel(const R* __restrict__ pos, R* __restrict__ out,
+                                  R* __restrict__ traj, long long off, long long traj_off, int T,
+                                  int M, int n_shift, int n_chains)
+{
+    const long long per = (long long)(T + 1) * M;
+    const long long n = (long long)n_chains * per;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e / per, le = e - b * per;
+        const long long src = le + (long long)n_shift * M;
+        if (src < per) out[off + b * per + le] = pos[off + b * per + src];
+        if (le >= M && le < (long long)(n_shift + 1) * M)
+            traj[traj_off + b * (long long)n_shift * M + (le - M)] = pos[off + b * per + le];
+    }
+}
+
+template <typename R>
+__global__ void regenerate_kernel(R* __restrict__ out, long long off, int T, int M, int n_shift,
+                                  int n_chains, int chain0, R sig, uint64_t seed, uint64_t counter,
+                                  const R* __restrict__ noise)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)n_chains * M) return;
+    const int b = (int)(g / M), m = (int)(g % M);
+    const long long per = (long long)(T + 1) * M;
+    R* X = out + off + b * per;
+    R x = X[(long long)(T - n_shift) * M + m];
+    for (int k = 1; k <= n_shift; ++k) {
+        const long long e = (long long)(k - 1) * M + m;  // index into this chain's [n_shift][M] noise
+        R z;
+        if (noise) {
+            z = noise[((long long)(chain0 + b)) * n_shift * M + e];
+        } else {
+            const float4 q = philox_normals4(seed, counter, kStreamRegenerate, (uint32_t)(chain0 + b),
+                                             (uint32_t)(e >> 2));
+            z = (R)pick4(q, (int)(e & 3));
+        }
+        x = x + sig * z;
+        X[(long long)(T - n_shift + k) * M + m] = x;
+    }
+}
+
+template <typename R>
+cudaError_t launch_shift_regenerate(const R* pos, R* out, R* traj, long long off, long long traj_off,
+                                    int T, int M, int n_shift, int n_chains, int chain0, double sig,
+                                    uint64_t seed, uint64_t counter, const R* noise, cudaStream_t st)
+{
+    if (n_chains <= 0) return cudaSuccess;
+    const long long n = (long long)n_chains * (T + 1) * M;
+    const int threads = 256;
+    const int blocks = (int)std::min<long long>((n + threads - 1) / threads, 152LL * 16);
+    shift_copy_kernel<R><<<blocks, threads, 0, st>>>(pos, out, traj, off, traj_off, T, M, n_shift,
+                                                     n_chains);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long nr = (long long)n_chains * M;
+    regenerate_kernel<R><<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(
+        out, off, T, M, n_shift, n_chains, chain0, (R)sig, seed, counter, noise);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_shift_regenerate<float>(const float*, float*, float*, long long, long long,
+                                                    int, int, int, int, int, double, uint64_t,
+                                                    uint64_t, const float*, cudaStream_t);
+template cudaError_t launch_shift_regenerate<double>(const double*, double*, double*, long long,
+                                                     long long, int, int, int, int, int, double,
+                                                     uint64_t, uint64_t, const double*, cudaStream_t);
 
 }  // namespace pamd

@@ -871,6 +871,39 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
     return PAMD_OK;
 }
 
+int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_out, int n_shift,
+                          void* traj, uint64_t seed, uint64_t counter, const void* noise,
+                          void* stream)
+{
+    NvtxRange nvtx_("pamd_shift_regenerate");
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!pos || !pos_out || !traj || pos == pos_out || n_shift < 1) return PAMD_ERR_ARG;
+    for (int q = 0; q < prob->n_systems; ++q)
+        if (n_shift > prob->systems[q].n_steps) return PAMD_ERR_ARG;
+    for (const void* ptr : {pos, (const void*)pos_out, (const void*)traj, noise})
+        if (ptr && is_host_ptr(ptr)) return PAMD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double sig = std::sqrt(2.0 * prob->D * prob->dt);
+    long long traj_off = 0;
+    int chain0 = 0;
+    for (int q = 0; q < prob->n_systems; ++q) {
+        const pamd_system& s = prob->systems[q];
+        const int M = s.dim * s.n_particles;
+        if (prob->precision == PAMD_FP64)
+            PAMD_CUDA_TRY(launch_shift_regenerate<double>(
+                (const double*)pos, (double*)pos_out, (double*)traj, s.pos_offset, traj_off, s.n_steps, M,
+                n_shift, s.n_chains, chain0, sig, seed, counter, (const double*)noise, st));
+        else
+            PAMD_CUDA_TRY(launch_shift_regenerate<float>(
+                (const float*)pos, (float*)pos_out, (float*)traj, s.pos_offset, traj_off, s.n_steps, M,
+                n_shift, s.n_chains, chain0, sig, seed, counter, (const float*)noise, st));
+        traj_off += (long long)s.n_chains * n_shift * M;
+        chain0 += s.n_chains;
+    }
+    return PAMD_OK;
+}
+
 int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* counts, void* stream)
 {
     NvtxRange nvtx_("pamd_lj_pair_counts");

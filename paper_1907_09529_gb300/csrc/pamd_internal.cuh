@@ -110,7 +110,8 @@ enum : uint32_t {
     kStreamAccept = 2,
     kStreamFragCut = 3,
     kStreamFragTrial = 4,
-    kStreamFragAccept = 5
+    kStreamFragAccept = 5,
+    kStreamRegenerate = 6
 };
 
 // ------------------------------------------------------------------ reductions
@@ -293,6 +294,13 @@ cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter,
                                    cudaStream_t st);
 
 cudaError_t launch_philox(uint4 ctr, uint2 key, long long n, uint32_t* out, cudaStream_t st);
+
+// Shift every chain of one system by n_shift steps into `out`, emit the
+// trajectory points, regrow the nose with free-particle steps.
+template <typename R>
+cudaError_t launch_shift_regenerate(const R* pos, R* out, R* traj, long long off, long long traj_off,
+                                    int T, int M, int n_shift, int n_chains, int chain0, double sig,
+                                    uint64_t seed, uint64_t counter, const R* noise, cudaStream_t st);
 
 // One multilevel sliding-and-sampling MC step of every chain of one harmonic
 // system (free-particle trials).

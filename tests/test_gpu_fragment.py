@@ -93,3 +93,53 @@ def test_fragment_mc_rejects_lennard_jones(pamd):
     with pytest.raises(pamd.PamdError) as ei:
         pamd.fragment_mc(prob, prob.empty("cuda"), 1, 2)
     assert ei.value.status == -2
+
+
+def test_shift_regenerate_matches_oracle(pamd):
+    from paper_1907_09529_gb300 import integrator
+    B, T, d, n_shift, D, dt = 3, 16, 2, 5, 0.7, 0.2
+    rng = inputs.rng(301)
+    prob = pamd.Problem([pamd.System("harmonic", 1, d, T, B)], D, 1.0, dt, precision="fp64")
+    paths = rng.standard_normal((B, T + 1, d, 1))
+    z = rng.standard_normal((B, n_shift, d, 1))
+    buf = prob.empty("cuda")
+    prob.view(buf, 0).copy_(torch.from_numpy(paths))
+    out = prob.empty("cuda")
+    traj = integrator.shift_regenerate(prob, buf, out, n_shift,
+                                       noise=torch.from_numpy(z.reshape(-1)).cuda())
+    torch.cuda.synchronize()
+    traj = traj.view(B, n_shift, d, 1).cpu().numpy()
+    got = prob.view(out, 0).cpu().numpy()
+    for b in range(B):
+        o, tr = oracle.shift_regenerate(paths[b], n_shift, z[b], D, dt)
+        assert np.abs(got[b] - o).max() <= 1e-13
+        assert np.array_equal(traj[b], tr)
+
+
+def test_pamd_loop_reproduces_the_euler_chain_statistics(pamd):
+    """The integrated trajectories of 4096 PAMD chains (N_path = 16, N_shift = 1,
+    N_sample = 16, levels 1..3, dt = 0.1) have the stationary variance
+    2 D dt / (1 - a^2) and lag-1 autocorrelation a = 1 - beta D k dt of the
+    Euler-Maruyama chain whose path measure the sampler draws from."""
+    from paper_1907_09529_gb300.integrator import PamdIntegrator
+    B, T, dt = 4096, 16, 0.1
+    prob = pamd.Problem([pamd.System("harmonic", 1, 1, T, B, k=1.0)], 1.0, 1.0, dt,
+                        precision="fp32")
+    buf = prob.empty("cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    prob.view(buf, 0).copy_(torch.randn(prob.view(buf, 0).shape, generator=g, device="cuda"))
+    integ = PamdIntegrator(prob, n_shift=1, n_sample=16, l_min=1, l_max=3, seed=77)
+    integ.run(buf, 300)  # equilibrate
+    traj = integ.run(buf, 1500).double().cpu().numpy()  # [events, chains]
+    a = 1 - dt
+    var_em = 2 * dt / (1 - a * a)
+    x = traj
+    v = (x ** 2).mean()
+    c1 = (x[1:] * x[:-1]).mean() / v
+    # effective samples ~ B * events / (2 tau), tau ~ 1/(1-a) = 10 steps
+    n_eff = B * x.shape[0] / 20
+    assert abs(v - var_em) < 6 * var_em * (2 / n_eff) ** 0.5 + 0.01 * var_em
+    assert abs(c1 - a) < 0.01
+    rate = float(integ.n_accepted.sum()) / float(integ.n_proposed.sum())
+    assert 0.3 < rate < 1.0
