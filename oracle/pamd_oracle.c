@@ -431,10 +431,13 @@ int or_mala_step(const or_potential* p, int N, int d, int T, double D, double be
  * exp(-S0) with S0 = sum |x_{t+1} - x_t|^2 / (4 D dt) (up to factors that do not
  * depend on the interior points), so
  *     log alpha = -(S(X') - S(X)) + (S0(X') - S0(X)),
- * both differences over the fragment's own steps.  Trial construction, step by
- * step with z[t+1][m] standard normals and sig = sqrt(2 D dt):
- *     bridge:  x'_{t+1} = x'_t + (x_b - x'_t)/(b - t) + sig sqrt((b-t-1)/(b-t)) z_{t+1}
- *     nose:    x'_{t+1} = x'_t + sig z_{t+1}.
+ * both differences over the fragment's own steps.  The trial starts from the
+ * free random walk W_t = sig (z_{a+1} + ... + z_t), t in (a, b], with z[t][m]
+ * standard normals and sig = sqrt(2 D dt):
+ *     nose:    x'_t = x_a + W_t
+ *     bridge:  x'_t = x_a + s (x_b - x_a) + (W_t - s W_b),   s = (t - a)/(b - a),
+ * the textbook Brownian bridge: a walk with its end pulled back to x_b by a
+ * linear correction (x'_b = x_b exactly).
  * log_u[f] decides fragment f (in order from the tail).  Returns the number of
  * fragments; *n_acc counts accepted fragments with interior points. */
 int or_fragment_step(const or_potential* p, int N, int d, int T, double D, double beta, double dt,
@@ -463,24 +466,30 @@ int or_fragment_step(const or_potential* p, int N, int d, int T, double D, doubl
         int nose = (f == nfrag - 1);
         if (!nose && fb - fa < 2) continue; /* no interior point */
         ++*n_prop;
-        /* trial path on [fa, fb] */
-        for (int m = 0; m < M; ++m) trial[(size_t)fa * M + m] = pos[(size_t)fa * M + m];
-        for (int t = fa; t < fb; ++t)
-            for (int m = 0; m < M; ++m) {
-                double xt = trial[(size_t)t * M + m];
-                double zz = z[(size_t)(t + 1) * M + m];
+        /* trial path on [fa, fb]: the walk W first (held in `trial`), then the
+         * bridge or nose built from it in place */
+        for (int m = 0; m < M; ++m) {
+            double xa = pos[(size_t)fa * M + m], xb = pos[(size_t)fb * M + m];
+            double W = 0.0;
+            for (int t = fa + 1; t <= fb; ++t) {
+                W += sig * z[(size_t)t * M + m];
+                trial[(size_t)t * M + m] = W;
+            }
+            double Wb = W;
+            trial[(size_t)fa * M + m] = xa;
+            for (int t = fa + 1; t <= fb; ++t) {
                 double y;
                 if (nose) {
-                    y = xt + sig * zz;
-                } else if (t + 1 == fb) {
-                    y = pos[(size_t)fb * M + m];
+                    y = xa + trial[(size_t)t * M + m];
+                } else if (t == fb) {
+                    y = xb;
                 } else {
-                    double xb = pos[(size_t)fb * M + m];
-                    double rem = (double)(fb - t);
-                    y = xt + (xb - xt) / rem + sig * sqrt((rem - 1.0) / rem) * zz;
+                    double sf = (double)(t - fa) / (double)(fb - fa);
+                    y = xa + sf * (xb - xa) + (trial[(size_t)t * M + m] - sf * Wb);
                 }
-                trial[(size_t)(t + 1) * M + m] = y;
+                trial[(size_t)t * M + m] = y;
             }
+        }
         /* action differences over the fragment's steps */
         double dS = 0.0, dS0 = 0.0;
         for (int t = fa; t < fb; ++t) {

@@ -471,3 +471,39 @@ def test_fragment_layout_and_fixed_endpoints():
         assert pos[e, 0, 0] == before[e, 0, 0]
     assert pos[16, 0, 0] != before[16, 0, 0]
     assert na == npr == 4  # [0,1] has no interior point
+
+
+def test_fragment_trials_are_free_particle_bridges_and_walks():
+    """With every fragment accepted the step returns its trial path.  Over many
+    normals its interior points follow the free-particle path distribution with
+    the fragment ends fixed (Sec. III): a Brownian bridge of covariance
+    2 D dt (t - a)(b - s)/(b - a) (t <= s) about the straight line between the
+    ends, and for the nose a random walk of covariance 2 D dt (min(t, s) - a)."""
+    T, D, dt, level, offset = 16, 0.7, 0.3, 3, 5   # fragments [0,5] [5,13] [13,16]
+    p = oracle.harmonic(1.0)
+    base = inputs.normals(41, (T + 1, 1, 1))
+    g = inputs.rng(42)
+    n = 40000
+    lu = np.full(oracle.n_fragments(T, level, offset), -np.inf)
+    out = np.empty((n, T + 1))
+    for i in range(n):
+        pos = base.copy()
+        nf, na, npr = oracle.fragment_step(p, pos, level, offset, g.standard_normal(pos.shape),
+                                           lu, D, 1.0, dt)
+        out[i] = pos[:, 0, 0]
+    assert nf == 3 and na == npr == 3
+    for e in (0, 5, 13):
+        assert np.all(out[:, e] == base[e, 0, 0])
+    x = base[:, 0, 0]
+    q = 2 * D * dt
+    for a, b, nose in ((0, 5, False), (5, 13, False), (13, 16, True)):
+        ts = np.arange(a + 1, b + 1 if nose else b)
+        ys = out[:, ts]
+        mean = np.full(len(ts), x[a]) if nose else x[a] + (ts - a) / (b - a) * (x[b] - x[a])
+        tt, ss = np.meshgrid(ts, ts, indexing="ij")
+        lo, hi = np.minimum(tt, ss), np.maximum(tt, ss)
+        cov = q * (lo - a) if nose else q * (lo - a) * (b - hi) / (b - a)
+        emp = np.cov(ys, rowvar=False)
+        sd = np.sqrt(np.diag(cov))
+        assert np.all(np.abs(ys.mean(0) - mean) < 5 * sd / math.sqrt(n))
+        assert np.all(np.abs(emp - cov) < 6 * np.outer(sd, sd) * math.sqrt(2.0 / n) + 1e-12)
