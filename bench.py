@@ -6,7 +6,8 @@ One step = one whole-path Metropolis-adjusted Langevin update of every chain
 path.  A step evaluates the action and gradient once per chain, so it processes
 N * T particle-timeslices per chain.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config lj500|ho3d|lj108|ragged|ho1d]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--config lj500|ho3d|lj108|ragged|ho1d|ho_pamd]
                   [--impl ours|reference]
 
 --impl reference times the CPU oracle (the slow plain FP64 program the GPU path
@@ -241,6 +242,91 @@ def max_over_ranks(ms: float, device=None) -> float:
     return float(t.item())
 
 
+def run_sampler(args, w, pamd, prob, dev, rank, world):
+    """PAMD integration (Fig. 2) with the multilevel sampler: one step = one
+    shifting event of every chain (n_sample MC steps + shift/regenerate)."""
+    import torch
+    from paper_1907_09529_gb300.integrator import PamdIntegrator
+    spec = w.systems[0]
+    n_shift, n_sample, l_min, l_max = 64, 1, 4, 8
+    if spec.T < 4096:
+        n_shift, l_min, l_max = 16, 2, 4
+    pos = prob.empty(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(rank_seed(w, rank))
+    prob.view(pos, 0).copy_(torch.randn(prob.view(pos, 0).shape, generator=g, device=dev))
+    integ = PamdIntegrator(prob, n_shift, n_sample, l_min, l_max, seed=rank_seed(w, rank))
+    integ.run(pos, max(1, args.warmup))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    integ.run(pos, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    clk = clocks.stop()
+    units = spec.N * spec.T * spec.n_chains * n_sample
+    value = aggregate(units, world, args.steps, ms)
+    # one-line paths that fit one CTA run the event as n_sample launches, the last
+    # of which also shifts and regrows the path: every MC step reads the path once
+    # and writes it once (accepted interiors, or the shifted path)
+    nbytes = spec.n_chains * (spec.T + 1) * 4 * 2 * n_sample
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    achieved = nbytes / (ms / args.steps * 1e-3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import numpy as np
+        import oracle
+        T = spec.T
+        pot = oracle.harmonic(spec.k)
+        x = np.random.default_rng(1).standard_normal((T + 1, 1, 1))
+        rng = np.random.default_rng(2)
+        t0, n = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 10.0:
+            l = int(rng.integers(l_min, l_max + 1))
+            o = int(rng.integers(0, 1 << l))
+            z = rng.standard_normal(x.shape)
+            lu = np.log(rng.random(oracle.n_fragments(T, l, o)))
+            oracle.fragment_step(pot, x, l, o, z, lu, w.D, w.beta, w.dt)
+            n += 1
+        dtm = time.perf_counter() - t0
+        cpu = {"value": n * T / dtm, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} multilevel MC steps of one chain (T={T}), {dtm:.1f} s"}
+    if rank == 0:
+        out = {"metric": "particle-timeslices/s sampled by the PAMD loop (multilevel MC + shift)",
+               "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": (f"ho_pamd: 1D harmonic oscillator, PAMD loop (Fig. 2) with "
+                                       f"the multilevel sampler (Sec. III), dt={w.dt}, "
+                                       f"N_path={spec.T}, N_sample={n_sample}, N_shift={n_shift}, "
+                                       f"levels {l_min}..{l_max}, {spec.n_chains} chains"),
+                          "units": "MD force evaluations of the sampler (N_sample * N_path per "
+                                   "chain per shifting event)",
+                          "l2": "inputs larger than L2" if nbytes / 2 > 129e6 else "L2-resident"},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "kernel": "fragment_line_kernel<float> (MC step + fused shift)",
+                            "peak_note": "of measured; algorithmic bytes = 8 per slice per MC "
+                                         "step (read + write); the kernel is issue-bound on "
+                                         "the Philox normals and scans, not on HBM"},
+               "cpu_baseline": cpu, "e2e": None,
+               "gpu_launches": args.steps * n_sample,
+               "clocks": clk,
+               "accept_rate": float(integ.n_accepted.sum()) / max(1.0, float(integ.n_proposed.sum()))}
+        print(json.dumps(out), flush=True)
+
+
 def launches_per_update(prob):
     n_lj = sum(1 for s in prob.systems if s.kind == "lj")
     n_ho = 1 if any(s.kind == "harmonic" for s in prob.systems) else 0
@@ -286,6 +372,11 @@ def main():
             systems.append(pamd.System("harmonic", s.N, s.d, s.T, s.n_chains, k=s.k))
     prob = pamd.Problem(systems, w.D, w.beta, w.dt, "fp32")
     stream = torch.cuda.current_stream(dev)
+    if w.name == "ho_pamd":
+        run_sampler(args, w, pamd, prob, dev, rank, world)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # Start paths, built on the device: Gaussian slices or Euler-Maruyama from FCC / 0.
     seed = rank_seed(w, rank)

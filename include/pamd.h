@@ -166,14 +166,17 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
  * x_T.  Each fragment is accepted or rejected on its own by Metropolis-Hastings
  * with a Brownian-bridge trial (random walk for the nose):
  *     log alpha = -(S(X') - S(X)) + (S0(X') - S0(X)),  S0 = free-particle action,
- * both over the fragment's steps, in double precision.
+ * both over the fragment's steps: per-step terms (r'-r)(r'+r) in the path's
+ * precision, fragment sums and the accept test in double.
  *   pos         : in/out, device buffer (precision's element type).
  *   l_min,l_max : 1 <= l_min <= l_max, 2^l_max <= T of every system.
  *   seed,counter: Philox key and counter (step u uses counter+u; streams 3-5:
  *                 level/offset from words 0/1 modulo the range, trial normals,
  *                 per-fragment 53-bit uniforms).
  *   levels, offsets : NULL, or (only with n_steps == 1) int[n_chains_total]
- *                 each, the fragmentation of every chain.
+ *                 each, the fragmentation of every chain; a chain whose level
+ *                 lies outside [l_min, l_max] or whose offset lies outside
+ *                 [0, 2^level) is left unchanged and proposes nothing.
  *   noise       : NULL, or (n_steps == 1) standard normals in the layout of pos;
  *                 slice t+1's entries drive the trial step t -> t+1.
  *   log_u       : NULL, or (n_steps == 1) double[n_chains_total * F] with
@@ -181,6 +184,10 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
  *                 from the tail) of chain c uses log_u[c*F + f].
  *   n_accepted, n_proposed : int[n_chains_total], incremented (fragments with
  *                 interior points are proposed).
+ * The trial of a fragment [a, b] is built from the walk
+ * W_t = sqrt(2 D dt) (z_{a+1} + ... + z_t): x_a + W_t for the nose, and
+ * x_a + s (x_b - x_a) + W_t - s W_b with s = (t-a)/(b-a) for a bridge.  A chain
+ * whose path (two copies) fits in shared memory is handled by one CTA.
  * Device pointers only (host pointers: PAMD_ERR_ARG); Lennard-Jones systems:
  * PAMD_ERR_UNSUPPORTED (their trial needs a hard-sphere pair propagator). */
 int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, int n_steps,
@@ -203,6 +210,25 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
 int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_out, int n_shift,
                           void* traj, uint64_t seed, uint64_t counter, const void* noise,
                           void* stream);
+
+/* One shifting event of the path-accelerated MD loop (paper Fig. 2) for every
+ * chain of harmonic systems: n_sample multilevel MC steps (as pamd_fragment_mc
+ * with counters event*n_sample + u, u = 0..n_sample-1), then the shift and
+ * regeneration (as pamd_shift_regenerate with counter `event`).  The results
+ * are bit-identical to that sequence of calls.  For one-line systems (dim*N
+ * == 1) whose path fits in shared memory the last MC step writes the shifted
+ * path, the trajectory points and the regrown nose itself, so the event reads
+ * and writes every path once.
+ *   pos      : in/out, the paths; on return the paths after the MC steps.
+ *   pos_out  : written, the shifted and regrown paths (another buffer).
+ *   traj     : written, x_1..x_{n_shift} of every chain (layout as in
+ *              pamd_shift_regenerate).
+ *   n_accepted, n_proposed : int[n_chains_total], incremented.
+ * Device pointers only; l_min, l_max and n_shift as in pamd_fragment_mc and
+ * pamd_shift_regenerate; Lennard-Jones systems: PAMD_ERR_UNSUPPORTED. */
+int pamd_event(const pamd_problem* prob, void* pos, void* pos_out, int n_sample, int n_shift,
+               int l_min, int l_max, void* traj, uint64_t seed, uint64_t event, int* n_accepted,
+               int* n_proposed, void* stream);
 
 /* Diagnostics for bit-exact index parity: number of ordered in-cutoff pairs
  * (i != j) of every slice of every LJ chain, decided in single precision by

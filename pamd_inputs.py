@@ -145,10 +145,19 @@ def workload(name: str, scale: Optional[str] = None) -> Workload:
             systems = ragged_lj_systems(s + 5)
         return Workload("ragged", systems, D=1.0, beta=1.0, dt=1e-4, init="euler",
                         n_updates=100, seed=s + 5)
+    if name == "ho_pamd":
+        # The oscillator of Sec. IV.A integrated by the PAMD loop of Fig. 2 with the
+        # multilevel sampler, in the shape of the paper's Simulation 3
+        # (dt = 0.4, N_path = 4096, N_sample = 1, N_shift = 64, levels 4..8).
+        B = 8 if small else 16384
+        T = 256 if small else 4096
+        return Workload("ho_pamd", [SystemSpec("harmonic", 1, 1, T, B)], D=1.0, beta=1.0,
+                        dt=0.4, init="gaussian", seed=s + 6,
+                        note="n_sample=1 n_shift=64 l_min=4 l_max=8")
     raise KeyError(name)
 
 
-WORKLOADS = ("ho1d", "ho3d", "lj108", "lj500", "ragged")
+WORKLOADS = ("ho1d", "ho3d", "lj108", "lj500", "ragged", "ho_pamd")
 
 
 def initial_positions(spec: SystemSpec, seed: int) -> np.ndarray:

@@ -18,7 +18,7 @@ import torch
 from . import _lib
 from ._lib import (PAMD_FLAG_ONE_CHAIN_PER_LAUNCH, PAMD_FP32, PAMD_FP64, PAMD_HARMONIC, PAMD_LJ,
                    PamdError, pamd_action, pamd_action_grad, pamd_device_status, pamd_euler_reference,
-                   pamd_fragment_mc, pamd_shift_regenerate,
+                   pamd_event, pamd_fragment_mc, pamd_shift_regenerate,
                    pamd_lj_pair_counts, pamd_normals, pamd_path_update, pamd_philox,
                    pamd_release_cache, pamd_tune, pamd_version)
 
@@ -28,7 +28,7 @@ __all__ = [
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_release_cache", "pamd_tune",
     "pamd_version", "pamd_device_status", "device_status", "pamd_fragment_mc", "fragment_mc",
-    "fragment_slots", "pamd_shift_regenerate",
+    "fragment_slots", "pamd_shift_regenerate", "pamd_event",
 ]
 
 ALIGN = 8  # system offsets are rounded to 8 elements (>= 16 bytes)

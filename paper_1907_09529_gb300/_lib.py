@@ -32,7 +32,7 @@ EXPORTS = (
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
-    "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate",
+    "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate", "pamd_event",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
                                                 u64, u64, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
             "pamd_shift_regenerate": (ctypes.c_int, [_PP, _VP, _VP, ctypes.c_int, _VP, u64, u64,
                                                      _VP, _VP]),
+            "pamd_event": (ctypes.c_int, [_PP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _VP, u64, u64, _VP, _VP, _VP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -166,6 +168,12 @@ def pamd_fragment_mc(prob, pos, l_min, l_max, n_steps, seed, counter, levels, of
 def pamd_shift_regenerate(prob, pos, pos_out, n_shift, traj, seed, counter, noise, stream):
     return _call("pamd_shift_regenerate", prob, pos, pos_out, n_shift, traj, seed, counter, noise,
                  stream)
+
+
+def pamd_event(prob, pos, pos_out, n_sample, n_shift, l_min, l_max, traj, seed, event,
+               n_accepted, n_proposed, stream):
+    return _call("pamd_event", prob, pos, pos_out, n_sample, n_shift, l_min, l_max, traj, seed,
+                 event, n_accepted, n_proposed, stream)
 
 
 def pamd_device_status(stream):

@@ -871,6 +871,70 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
     return PAMD_OK;
 }
 
+int pamd_event(const pamd_problem* prob, void* pos, void* pos_out, int n_sample, int n_shift,
+               int l_min, int l_max, void* traj, uint64_t seed, uint64_t event, int* n_accepted,
+               int* n_proposed, void* stream)
+{
+    NvtxRange nvtx_("pamd_event");
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!pos || !pos_out || !traj || pos == pos_out || !n_accepted || !n_proposed || n_sample < 1 ||
+        n_shift < 1 || l_min < 1 || l_max < l_min || l_max > 30)
+        return PAMD_ERR_ARG;
+    int Tmax = 0;
+    for (int q = 0; q < prob->n_systems; ++q) {
+        const pamd_system& s = prob->systems[q];
+        if (s.pot.kind != PAMD_HARMONIC) return PAMD_ERR_UNSUPPORTED;
+        if ((1LL << l_max) > s.n_steps || n_shift > s.n_steps) return PAMD_ERR_ARG;
+        Tmax = std::max(Tmax, s.n_steps);
+    }
+    for (const void* ptr : {(const void*)pos, (const void*)pos_out, (const void*)traj,
+                            (const void*)n_accepted, (const void*)n_proposed})
+        if (is_host_ptr(ptr)) return PAMD_ERR_ARG;
+    const int fstride = (Tmax >> l_min) + 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double a = prob->beta * prob->D * prob->dt, sig = std::sqrt(2.0 * prob->D * prob->dt);
+    const double c4 = 1.0 / (4.0 * prob->D * prob->dt);
+    const bool fp64 = prob->precision == PAMD_FP64;
+    long long traj_off = 0;
+    int chain0 = 0;
+    for (int q = 0; q < prob->n_systems; ++q) {
+        const pamd_system& s = prob->systems[q];
+        const int M = s.dim * s.n_particles, T = s.n_steps;
+        const bool fuse = fp64 ? fragment_event_fusable<double>(T, M, l_min, n_shift)
+                               : fragment_event_fusable<float>(T, M, l_min, n_shift);
+        for (int u = 0; u < n_sample; ++u) {
+            const uint64_t ctr = event * (uint64_t)n_sample + (uint64_t)u;
+            const bool last = fuse && u == n_sample - 1;
+            if (fp64)
+                PAMD_CUDA_TRY(launch_fragment_mc<double>(
+                    (double*)pos, s.pos_offset, T, M, s.n_chains, chain0, s.pot.k, l_min, l_max, seed,
+                    ctr, nullptr, nullptr, nullptr, nullptr, fstride, a, sig, c4, n_accepted,
+                    n_proposed, st, last ? (double*)pos_out : nullptr,
+                    last ? (double*)traj + traj_off : nullptr, n_shift, event));
+            else
+                PAMD_CUDA_TRY(launch_fragment_mc<float>(
+                    (float*)pos, s.pos_offset, T, M, s.n_chains, chain0, s.pot.k, l_min, l_max, seed,
+                    ctr, nullptr, nullptr, nullptr, nullptr, fstride, a, sig, c4, n_accepted,
+                    n_proposed, st, last ? (float*)pos_out : nullptr,
+                    last ? (float*)traj + traj_off : nullptr, n_shift, event));
+        }
+        if (!fuse) {
+            if (fp64)
+                PAMD_CUDA_TRY(launch_shift_regenerate<double>(
+                    (const double*)pos, (double*)pos_out, (double*)traj, s.pos_offset, traj_off, T, M,
+                    n_shift, s.n_chains, chain0, sig, seed, event, nullptr, st));
+            else
+                PAMD_CUDA_TRY(launch_shift_regenerate<float>(
+                    (const float*)pos, (float*)pos_out, (float*)traj, s.pos_offset, traj_off, T, M,
+                    n_shift, s.n_chains, chain0, sig, seed, event, nullptr, st));
+        }
+        traj_off += (long long)s.n_chains * n_shift * M;
+        chain0 += s.n_chains;
+    }
+    return PAMD_OK;
+}
+
 int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_out, int n_shift,
                           void* traj, uint64_t seed, uint64_t counter, const void* noise,
                           void* stream)

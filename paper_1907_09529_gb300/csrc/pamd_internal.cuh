@@ -44,6 +44,12 @@ __device__ __forceinline__ float fma_r(float a, float b, float c) { return __fma
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_r(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_r(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_r(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_r(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float div_r(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_r(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
 
@@ -304,12 +310,22 @@ cudaError_t launch_shift_regenerate(const R* pos, R* out, R* traj, long long off
 
 // One multilevel sliding-and-sampling MC step of every chain of one harmonic
 // system (free-particle trials).
+// Largest shared-memory footprint of the one-CTA-per-chain fragment kernel;
+// larger chains take the one-thread-per-fragment kernel.
+constexpr size_t kFragBlockSmemMax = 192 * 1024;
+
+template <typename R>
+bool fragment_event_fusable(int T, int M, int l_min, int n_shift);
+// shift_out != nullptr: fuse the shift epilogue of a shifting event (one-line
+// systems only, see fragment_event_fusable)
 template <typename R>
 cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains, int chain0,
                                double k, int l_min, int l_max, uint64_t seed, uint64_t counter,
                                const int* levels, const int* offsets, const R* noise,
                                const double* log_u, int fstride, double a, double sig, double c4,
-                               int* n_accepted, int* n_proposed, cudaStream_t st);
+                               int* n_accepted, int* n_proposed, cudaStream_t st,
+                               R* shift_out = nullptr, R* shift_traj = nullptr, int n_shift = 0,
+                               uint64_t shift_counter = 0);
 cudaError_t launch_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain,
                            long long e0, long long n, float* out, cudaStream_t st);
 

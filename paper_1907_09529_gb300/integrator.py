@@ -13,7 +13,7 @@ from typing import Optional
 
 import torch
 
-from . import Problem, _check_buf, _ptr, _stream, fragment_mc, pamd_shift_regenerate
+from . import Problem, _check_buf, _ptr, _stream, pamd_event, pamd_shift_regenerate
 
 
 def shift_regenerate(p: Problem, pos: torch.Tensor, pos_out: torch.Tensor, n_shift: int,
@@ -29,6 +29,18 @@ def shift_regenerate(p: Problem, pos: torch.Tensor, pos_out: torch.Tensor, n_shi
     pamd_shift_regenerate(p.ref, _ptr(pos), _ptr(pos_out), int(n_shift), _ptr(traj), int(seed),
                           int(counter), _ptr(noise), _stream(pos, stream))
     return traj
+
+
+def event(p: Problem, pos: torch.Tensor, pos_out: torch.Tensor, n_sample: int, n_shift: int,
+          l_min: int, l_max: int, traj: torch.Tensor, n_accepted: torch.Tensor,
+          n_proposed: torch.Tensor, seed: int = 0, event: int = 0, stream=None) -> None:
+    """One shifting event (Fig. 2): n_sample MC steps on `pos`, then the shifted
+    and regrown paths into `pos_out` and the trajectory points into `traj`."""
+    _check_buf(p, pos, "pos")
+    _check_buf(p, pos_out, "pos_out")
+    pamd_event(p.ref, _ptr(pos), _ptr(pos_out), int(n_sample), int(n_shift), int(l_min), int(l_max),
+               _ptr(traj), int(seed), int(event), _ptr(n_accepted), _ptr(n_proposed),
+               _stream(pos, stream))
 
 
 class PamdIntegrator:
@@ -54,11 +66,8 @@ class PamdIntegrator:
         out = torch.empty((n_events, per), dtype=p.dtype, device=pos.device)
         a, b = pos, torch.empty_like(pos)
         for ev in range(n_events):
-            k = self.events + ev
-            fragment_mc(p, a, self.l_min, self.l_max, self.n_sample, seed=self.seed,
-                        counter=k * self.n_sample, n_accepted=self.n_accepted,
-                        n_proposed=self.n_proposed)
-            shift_regenerate(p, a, b, self.n_shift, traj=out[ev], seed=self.seed, counter=k)
+            event(p, a, b, self.n_sample, self.n_shift, self.l_min, self.l_max, out[ev],
+                  self.n_accepted, self.n_proposed, seed=self.seed, event=self.events + ev)
             a, b = b, a
         if a is not pos:
             pos.copy_(a)

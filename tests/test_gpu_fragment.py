@@ -28,6 +28,11 @@ def pamd():
     ("fp64", 256, 1, 4, 5, 0.4),    # Simulation 2 shape
     ("fp64", 1024, 3, 2, 6, 0.01),
     ("fp32", 256, 1, 4, 5, 0.4),
+    ("fp32", 4096, 1, 4, 8, 0.4),   # Simulation 3 shape
+    ("fp32", 2048, 1, 3, 7, 0.4),   # 5 warps per chain
+    ("fp32", 1000, 1, 1, 4, 0.1),   # level 1: up to three fragments per quad
+    ("fp64", 40000, 1, 5, 9, 0.4),  # too large for one CTA: thread-per-fragment kernel
+    ("fp32", 30000, 2, 3, 6, 0.05),
 ])
 def test_fragment_step_matches_oracle(pamd, precision, T, d, l_min, l_max, dt):
     B, D, beta = 4, 1.0, 1.0
@@ -143,3 +148,117 @@ def test_pamd_loop_reproduces_the_euler_chain_statistics(pamd):
     assert abs(c1 - a) < 0.01
     rate = float(integ.n_accepted.sum()) / float(integ.n_proposed.sum())
     assert 0.3 < rate < 1.0
+
+
+def test_fragment_mc_skips_invalid_cuts(pamd):
+    """A chain given a level outside [l_min, l_max] or an offset outside
+    [0, 2^level) keeps its path and proposes nothing; the others still move."""
+    B, T = 4, 64
+    prob = pamd.Problem([pamd.System("harmonic", 1, 1, T, B)], 1.0, 1.0, 0.1, precision="fp64")
+    rng = inputs.rng(404)
+    paths = rng.standard_normal((B, T + 1, 1, 1))
+    buf = prob.empty("cuda")
+    prob.view(buf, 0).copy_(torch.from_numpy(paths))
+    levels = torch.tensor([1, 5, 3, 3], dtype=torch.int32, device="cuda")
+    offsets = torch.tensor([0, 0, 8, -1], dtype=torch.int32, device="cuda")
+    F = pamd.fragment_slots(prob, 2)
+    log_u = torch.full((B * F,), -np.inf, dtype=torch.float64, device="cuda")  # accept all
+    acc, prop = pamd.fragment_mc(prob, buf, 2, 4, 1, levels=levels, offsets=offsets,
+                                 log_u=log_u)
+    torch.cuda.synchronize()
+    got = prob.view(buf, 0).cpu().numpy()
+    assert prop.tolist() == [0, 0, 0, 0] and acc.tolist() == [0, 0, 0, 0]
+    assert np.array_equal(got, paths)
+    levels[1], offsets[1] = 4, 15
+    acc, prop = pamd.fragment_mc(prob, buf, 2, 4, 1, levels=levels, offsets=offsets,
+                                 log_u=log_u)
+    torch.cuda.synchronize()
+    got = prob.view(buf, 0).cpu().numpy()
+    assert prop.tolist() == [0, 5, 0, 0] and acc.tolist() == [0, 5, 0, 0]
+    assert np.array_equal(got[[0, 2, 3]], paths[[0, 2, 3]])
+    assert not np.array_equal(got[1, 16:], paths[1, 16:])
+
+
+def _philox_log_u(seed, counter, chain, f):
+    w = oracle.philox([f, chain, counter & 0xFFFFFFFF, ((counter >> 32) & 0xFFFF) | (5 << 16)],
+                      [seed & 0xFFFFFFFF, seed >> 32])
+    mant = (int(w[0]) >> 5) * 67108864 + (int(w[1]) >> 6)
+    return math.log((mant + 1.0) * 2.0 ** -53)
+
+
+def test_fragment_mc_full_size_sampled_chains(pamd):
+    """The Simulation 3 shape at full batch (16384 chains, N_path = 4096,
+    levels 4..8, Philox-driven): sampled chains match the oracle fed with the
+    same Philox cut (stream 3), trial normals (stream 4) and uniforms (stream 5)."""
+    w = inputs.workload("ho_pamd")
+    spec = w.systems[0]
+    B, T = spec.n_chains, spec.T
+    l_min, l_max, seed, counter = 4, 8, 0x5EED1907, 11
+    prob = pamd.Problem([pamd.System("harmonic", 1, 1, T, B)], w.D, w.beta, w.dt,
+                        precision="fp32")
+    buf = prob.empty("cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    prob.view(buf, 0).copy_(torch.randn(prob.view(buf, 0).shape, generator=g, device="cuda"))
+    before = prob.view(buf, 0).double().cpu().numpy()
+    acc, prop = pamd.fragment_mc(prob, buf, l_min, l_max, 1, seed=seed, counter=counter)
+    torch.cuda.synchronize()
+    after = prob.view(buf, 0).double().cpu().numpy()
+    pot = oracle.harmonic(1.0)
+    rng = inputs.rng(77)
+    sample = sorted(set(rng.integers(0, B, size=24).tolist()) | {0, B - 1})
+    for c in sample:
+        wc = oracle.philox([0, c, counter, 3 << 16], [seed & 0xFFFFFFFF, seed >> 32])
+        l = l_min + int(wc[0]) % (l_max - l_min + 1)
+        o = int(wc[1]) % (1 << l)
+        nf = oracle.n_fragments(T, l, o)
+        z = oracle.normals(seed, counter, 4, c, T + 1).astype(np.float32).astype(np.float64)
+        lu = np.array([_philox_log_u(seed, counter, c, f) for f in range(nf)])
+        x = before[c].copy()
+        _, na, npr = oracle.fragment_step(pot, x, l, o, z.reshape(T + 1, 1, 1), lu,
+                                          w.D, w.beta, w.dt)
+        assert (int(acc[c]), int(prop[c])) == (na, npr), c
+        assert np.abs(after[c] - x).max() <= 2e-5 * max(1.0, np.abs(x).max()), c
+    assert float(acc.sum()) > 0
+
+
+@pytest.mark.parametrize("precision,d,T,n_sample,n_shift,l_min,l_max", [
+    ("fp32", 1, 4096, 1, 64, 4, 8),    # fused epilogue (one-line paths)
+    ("fp32", 1, 256, 3, 16, 2, 5),
+    ("fp64", 1, 1024, 2, 7, 3, 6),
+    ("fp32", 3, 512, 2, 10, 2, 4),     # several lines: separate shift kernels
+    ("fp64", 1, 40000, 1, 33, 5, 9),   # too large for one CTA: separate kernels
+])
+def test_event_matches_separate_calls(pamd, precision, d, T, n_sample, n_shift, l_min, l_max):
+    """pamd_event equals n_sample pamd_fragment_mc steps followed by
+    pamd_shift_regenerate, bit for bit, for paths, trajectory and counts."""
+    from paper_1907_09529_gb300 import integrator
+    B, seed, ev = 5, 97531, 3
+    prob = pamd.Problem([pamd.System("harmonic", 1, d, T, B),
+                         pamd.System("harmonic", 1, d, T // 2, 2)], 1.0, 1.0, 0.3,
+                        precision=precision)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    a = prob.empty("cuda")
+    for q in range(2):
+        prob.view(a, q).copy_(torch.randn(prob.view(a, q).shape, generator=g, device="cuda"))
+    a2 = a.clone()
+    n = sum(s.n_chains * n_shift * s.d * s.N for s in prob.systems)
+    acc1 = torch.zeros(prob.n_chains, dtype=torch.int32, device="cuda")
+    prop1 = torch.zeros_like(acc1)
+    acc2, prop2 = acc1.clone(), prop1.clone()
+    out1, out2 = prob.empty("cuda"), prob.empty("cuda")
+    traj1 = torch.empty(n, dtype=prob.dtype, device="cuda")
+    traj2 = torch.empty_like(traj1)
+    pamd.fragment_mc(prob, a, l_min, l_max, n_sample, seed=seed, counter=ev * n_sample,
+                     n_accepted=acc1, n_proposed=prop1)
+    integrator.shift_regenerate(prob, a, out1, n_shift, traj=traj1, seed=seed, counter=ev)
+    integrator.event(prob, a2, out2, n_sample, n_shift, l_min, l_max, traj2, acc2, prop2,
+                     seed=seed, event=ev)
+    torch.cuda.synchronize()
+    for q in range(2):
+        assert torch.equal(prob.view(a, q), prob.view(a2, q))
+        assert torch.equal(prob.view(out1, q), prob.view(out2, q))
+    assert torch.equal(traj1, traj2)
+    assert torch.equal(acc1, acc2) and torch.equal(prop1, prop2)
+    assert int(prop1.sum()) > 0
