@@ -136,9 +136,17 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def kernel_source_hash():
+#: Sources that define each profiled kernel (with the shared header).
+KERNEL_SOURCES = {
+    "lj_action_kernel": ("lj_kernels.cu", "pamd_internal.cuh"),
+    "ho_vec_kernel": ("ho_kernels.cu", "pamd_internal.cuh"),
+    "fragment_line_kernel": ("fragment_kernels.cu", "pamd_internal.cuh"),
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in ("lj_kernels.cu", "ho_kernels.cu", "pamd_internal.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1907_09529_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -146,14 +154,14 @@ def kernel_source_hash():
 
 def profiled_traffic(config, kernel):
     """DRAM bytes per launch recorded from an ncu capture of the current kernel source
-    (profiles/traffic.json), or None if the kernels changed since."""
+    (profiles/traffic.json), or None if the kernel's sources changed since."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
     ent = rec.get(config, {})
-    if ent.get("kernel") != kernel or ent.get("source_hash") != kernel_source_hash():
+    if ent.get("kernel") != kernel or ent.get("source_hash") != kernel_source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -315,7 +323,8 @@ def run_sampler(args, w, pamd, prob, dev, rank, world):
                                    "chain per shifting event)",
                           "l2": "inputs larger than L2" if nbytes / 2 > 129e6 else "L2-resident"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "traffic": None,
+                            "frac": achieved / peak,
+                            "traffic": profiled_traffic("ho_pamd", "fragment_line_kernel"),
                             "kernel": "fragment_line_kernel<float> (MC step + fused shift)",
                             "peak_note": "of measured; algorithmic bytes = 8 per slice per MC "
                                          "step (read + write); the kernel is issue-bound on "

@@ -507,3 +507,27 @@ def test_fragment_trials_are_free_particle_bridges_and_walks():
         sd = np.sqrt(np.diag(cov))
         assert np.all(np.abs(ys.mean(0) - mean) < 5 * sd / math.sqrt(n))
         assert np.all(np.abs(emp - cov) < 6 * np.outer(sd, sd) * math.sqrt(2.0 / n) + 1e-12)
+
+
+def test_shift_regenerate_grows_free_particle_walks():
+    """Shift and regeneration (Fig. 2B): the kept slices move n_shift steps
+    toward the tail, the trajectory gets x_1..x_{n_shift}, and the regrown nose
+    is a free-particle random walk from the old nose: over many draws its mean
+    is x_T and its covariance 2 D dt min(i, j) (the sampler's trial
+    distribution, Sec. III)."""
+    T, n_shift, D, dt = 12, 5, 0.6, 0.25
+    pos = inputs.normals(61, (T + 1, 1, 1))
+    g = inputs.rng(62)
+    n = 40000
+    nose = np.empty((n, n_shift))
+    for i in range(n):
+        out, traj = oracle.shift_regenerate(pos, n_shift, g.standard_normal((n_shift, 1, 1)), D, dt)
+        if i == 0:
+            assert np.array_equal(out[:T - n_shift + 1], pos[n_shift:])
+            assert np.array_equal(traj, pos[1:n_shift + 1])
+        nose[i] = out[T - n_shift + 1:, 0, 0]
+    ks = np.arange(1, n_shift + 1)
+    cov = 2 * D * dt * np.minimum.outer(ks, ks)
+    sd = np.sqrt(np.diag(cov))
+    assert np.all(np.abs(nose.mean(0) - pos[T, 0, 0]) < 5 * sd / math.sqrt(n))
+    assert np.all(np.abs(np.cov(nose, rowvar=False) - cov) < 6 * np.outer(sd, sd) * math.sqrt(2.0 / n))
