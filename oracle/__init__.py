@@ -101,7 +101,7 @@ def _load():
                                      _D, c_double, _D, _D, c_double, c_int, _D, _D, _D, _D, _I,
                                      c_int]),
             "or_fragment_step": (c_int, [_P, c_int, c_int, c_int, c_double, c_double, c_double,
-                                         c_int, c_int, _D, _D, _D, _I, _I]),
+                                         c_int, c_int, _D, _D, _D, _I, _I, c_int]),
             "or_shift_regenerate": (None, [c_int, c_int, c_int, c_double, c_double, c_int, _D, _D,
                                            _D, _D]),
             "or_philox4x32_10": (None, [_U32, _U32, _U32]),
@@ -270,10 +270,11 @@ def mala_step(pot: Potential, pos: np.ndarray, S: float, grad: np.ndarray, eta: 
 
 
 def fragment_step(pot: Potential, pos: np.ndarray, level: int, offset: int, z: np.ndarray,
-                  log_u, D: float, beta: float, dt: float):
+                  log_u, D: float, beta: float, dt: float, exact_ho: bool = False):
     """One multilevel sliding-and-sampling MC step (Sec. III, Fig. 5) with
     free-particle trials; pos [T+1][d][N] is updated in place.  z has the layout
     of pos (slice-0 entries unused); log_u holds one log uniform per fragment.
+    exact_ho: the oscillator's exact transition density in place of Eq. (3).
     Returns (n_fragments, n_accepted, n_proposed)."""
     assert pos.dtype == np.float64 and pos.flags.c_contiguous
     T = pos.shape[0] - 1
@@ -282,7 +283,10 @@ def fragment_step(pot: Potential, pos: np.ndarray, level: int, offset: int, z: n
     lu = _f64(log_u)
     acc, prop = ctypes.c_int(0), ctypes.c_int(0)
     nf = _load().or_fragment_step(ctypes.byref(pot), N, d, T, D, beta, dt, int(level), int(offset),
-                                  _d(z), _d(lu), _d(pos), ctypes.byref(acc), ctypes.byref(prop))
+                                  _d(z), _d(lu), _d(pos), ctypes.byref(acc), ctypes.byref(prop),
+                                  int(bool(exact_ho)))
+    if nf == -2:
+        raise ValueError("exact_ho needs the harmonic potential")
     if nf < 0:
         raise MemoryError("oracle fragment_step")
     return nf, acc.value, prop.value

@@ -439,13 +439,23 @@ int or_mala_step(const or_potential* p, int N, int d, int T, double D, double be
  * the textbook Brownian bridge: a walk with its end pulled back to x_b by a
  * linear correction (x'_b = x_b exactly).
  * log_u[f] decides fragment f (in order from the tail).  Returns the number of
- * fragments; *n_acc counts accepted fragments with interior points. */
+ * fragments; *n_acc counts accepted fragments with interior points.
+ *
+ * exact_ho = 1 (harmonic potential only) replaces the short-time propagator of
+ * Eq. (3) in S by the exact transition density of the overdamped oscillator
+ * (the marginal of Sec. II for V = k x^2 / 2, with gamma^-1 = beta D):
+ *     K(x'|x) ~ exp(-(beta k / 2) |x' - phi x|^2 / (1 - phi^2)),  phi = exp(-beta D k dt),
+ * so each step contributes |x' - phi x|^2 beta k / (2 (1 - phi^2)).  The trial
+ * distribution and S0 are unchanged. */
 int or_fragment_step(const or_potential* p, int N, int d, int T, double D, double beta, double dt,
                      int level, int offset, const double* z, const double* log_u, double* pos,
-                     int* n_acc, int* n_prop)
+                     int* n_acc, int* n_prop, int exact_ho)
 {
     int M = d * N;
     double a = beta * D * dt, sig = sqrt(2.0 * D * dt), c4 = 1.0 / (4.0 * D * dt);
+    if (exact_ho && p->kind != OR_HARMONIC) return -2;
+    double phi = exp(-beta * D * p->k * dt);
+    double cx = beta * p->k / (2.0 * (1.0 - phi * phi));
     int len = 1 << level;
     double* trial = (double*)malloc(sizeof(double) * (size_t)(T + 1) * M);
     double* F = (double*)malloc(sizeof(double) * (size_t)M);
@@ -498,8 +508,13 @@ int or_fragment_step(const or_potential* p, int N, int d, int T, double D, doubl
             for (int m = 0; m < M; ++m) {
                 double x0 = pos[(size_t)t * M + m], x1 = pos[(size_t)(t + 1) * M + m];
                 double y0 = trial[(size_t)t * M + m], y1 = trial[(size_t)(t + 1) * M + m];
-                double r = x1 - x0 - a * F[m], rt = y1 - y0 - a * Ft[m];
-                dS += (rt * rt - r * r) * c4;
+                if (exact_ho) {
+                    double r = x1 - phi * x0, rt = y1 - phi * y0;
+                    dS += (rt * rt - r * r) * cx;
+                } else {
+                    double r = x1 - x0 - a * F[m], rt = y1 - y0 - a * Ft[m];
+                    dS += (rt * rt - r * r) * c4;
+                }
                 dS0 += ((y1 - y0) * (y1 - y0) - (x1 - x0) * (x1 - x0)) * c4;
             }
         }

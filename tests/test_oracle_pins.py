@@ -246,7 +246,8 @@ def test_mala_samples_the_path_distribution():
     assert 0.3 < acc / n_steps < 0.98
     for col, t in enumerate((4, 8)):
         m = a ** t * x0v
-        v = 2 * dt * (1 - a ** (2 * t)) / (1 - a ** 2)
+        step_var = (1 - a * a) if exact else 2 * dt
+        v = step_var * (1 - a ** (2 * t)) / (1 - a ** 2)
         xs = samples[:, col]
         nb = 50
         bm = xs[: len(xs) // nb * nb].reshape(nb, -1).mean(1)
@@ -416,14 +417,18 @@ def test_pair_count_f32_agrees_with_exact_distances():
 
 # ---------------------------------------------------------------- multilevel sliding-and-sampling MC
 @pytest.mark.slow
-@pytest.mark.parametrize("levels", [(1, 1), (2, 3)])
-def test_fragment_mc_samples_the_path_distribution(levels):
+@pytest.mark.parametrize("levels,exact,dt", [((1, 1), False, 0.1), ((2, 3), False, 0.1),
+                                             ((2, 3), True, 0.4)])
+def test_fragment_mc_samples_the_path_distribution(levels, exact, dt):
     """Repeated multilevel fragment MC steps (free-particle trials) leave the
     oscillator path distribution exp(-S) with x_0 fixed invariant: sampled x_4
-    and x_8 match the exact AR(1) marginals of the Euler-Maruyama chain."""
-    T, dt, x0v = 8, 0.1, 1.0
+    and x_8 match the exact AR(1) marginals of the chain S describes -- the
+    Euler-Maruyama chain (coefficient 1 - dt) for Eq. (3), the exact
+    Ornstein-Uhlenbeck transition (coefficient e^{-dt}, variance 1 - e^{-2t}
+    at time t) for the oscillator's exact propagator."""
+    T, x0v = 8, 1.0
     p = oracle.harmonic(1.0)
-    a = 1 - dt
+    a = math.exp(-dt) if exact else 1 - dt
     pos = np.zeros((T + 1, 1, 1))
     pos[0] = x0v
     g = inputs.rng(91 + levels[0])
@@ -436,7 +441,7 @@ def test_fragment_mc_samples_the_path_distribution(levels):
         z = g.standard_normal(pos.shape)
         nf = oracle.n_fragments(T, l, o)
         lu = np.log(g.random(nf))
-        nf2, na, npr = oracle.fragment_step(p, pos, l, o, z, lu, 1.0, 1.0, dt)
+        nf2, na, npr = oracle.fragment_step(p, pos, l, o, z, lu, 1.0, 1.0, dt, exact_ho=exact)
         assert nf2 == nf
         acc += na
         prop += npr
@@ -447,7 +452,8 @@ def test_fragment_mc_samples_the_path_distribution(levels):
     samples = np.array(samples)
     for col, t in enumerate((4, 8)):
         m = a ** t * x0v
-        v = 2 * dt * (1 - a ** (2 * t)) / (1 - a ** 2)
+        step_var = (1 - a * a) if exact else 2 * dt
+        v = step_var * (1 - a ** (2 * t)) / (1 - a ** 2)
         xs = samples[:, col]
         nb = 50
         k = len(xs) // nb * nb
