@@ -246,8 +246,7 @@ def test_mala_samples_the_path_distribution():
     assert 0.3 < acc / n_steps < 0.98
     for col, t in enumerate((4, 8)):
         m = a ** t * x0v
-        step_var = (1 - a * a) if exact else 2 * dt
-        v = step_var * (1 - a ** (2 * t)) / (1 - a ** 2)
+        v = 2 * dt * (1 - a ** (2 * t)) / (1 - a ** 2)
         xs = samples[:, col]
         nb = 50
         bm = xs[: len(xs) // nb * nb].reshape(nb, -1).mean(1)
