@@ -107,6 +107,17 @@ typedef struct {
 
 /* Run one chain per launch (the "plain" single-path form). */
 #define PAMD_FLAG_ONE_CHAIN_PER_LAUNCH 1
+/* Multilevel sampler and PAMD loop only (pamd_fragment_mc, pamd_event): the
+ * harmonic systems' path action uses the oscillator's exact transition
+ * density (the marginal of Sec. II for V = k|x|^2/2, gamma^-1 = beta D),
+ *     S = sum_t |x_{t+1} - phi x_t|^2 beta k / (2 (1 - phi^2)),  phi = exp(-beta D k dt),
+ * in place of Eq. (3); trials and regeneration are unchanged.  The action,
+ * gradient, update and Euler entry points reject it (PAMD_ERR_UNSUPPORTED). */
+#define PAMD_FLAG_HO_EXACT_PROPAGATOR 2
+/* Shift and regeneration (pamd_shift_regenerate, pamd_event): continue the
+ * path past the nose as the horizontal straight line x_T (Fig. 2B's
+ * straight-line regeneration, zero slope) instead of free-particle steps. */
+#define PAMD_FLAG_REGENERATE_FLAT 4
 
 /* Action S of every chain (Eqs. (3)-(4)).
  *   pos : path buffer (precision's element type), layout above.
@@ -201,7 +212,8 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
  *   pos_out : another path buffer of the same layout, written: slices
  *             0..T-n_shift are pos's slices n_shift..T; the last n_shift slices
  *             continue from the nose by free-particle steps x + sqrt(2 D dt) z
- *             (the sampler's trial distribution).
+ *             (the sampler's trial distribution), or hold x_T with
+ *             PAMD_FLAG_REGENERATE_FLAT.
  *   traj    : written, the trajectory points x_1..x_{n_shift} of every chain:
  *             [chains][n_shift][dim][N] per system, systems one after another.
  *   noise   : NULL (Philox stream 6, seed/counter) or standard normals

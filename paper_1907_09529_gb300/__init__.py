@@ -16,7 +16,8 @@ from typing import List, Optional, Sequence
 import torch
 
 from . import _lib
-from ._lib import (PAMD_FLAG_ONE_CHAIN_PER_LAUNCH, PAMD_FP32, PAMD_FP64, PAMD_HARMONIC, PAMD_LJ,
+from ._lib import (PAMD_FLAG_HO_EXACT_PROPAGATOR, PAMD_FLAG_ONE_CHAIN_PER_LAUNCH,
+                   PAMD_FLAG_REGENERATE_FLAT, PAMD_FP32, PAMD_FP64, PAMD_HARMONIC, PAMD_LJ,
                    PamdError, pamd_action, pamd_action_grad, pamd_device_status, pamd_euler_reference,
                    pamd_event, pamd_fragment_mc, pamd_shift_regenerate,
                    pamd_lj_pair_counts, pamd_normals, pamd_path_update, pamd_philox,
@@ -57,7 +58,13 @@ class Problem:
     """A batch of systems sharing D, beta, dt, laid out in one flat buffer."""
 
     def __init__(self, systems: Sequence[System], D: float, beta: float, dt: float,
-                 precision: str = "fp32", one_chain_per_launch: bool = False):
+                 precision: str = "fp32", one_chain_per_launch: bool = False,
+                 ho_exact_propagator: bool = False, regenerate_flat: bool = False):
+        """ho_exact_propagator: the sampler and the PAMD loop use the oscillator's
+        exact transition density as the path action (the action, gradient and
+        update entry points then refuse the problem).  regenerate_flat: the
+        shift continues the path past the nose as the line x_T instead of
+        free-particle steps."""
         self.systems: List[System] = list(systems)
         self.D, self.beta, self.dt = float(D), float(beta), float(dt)
         self.precision = precision
@@ -82,6 +89,10 @@ class Problem:
                                       _lib.pamd_potential(kind, s.k, s.eps, s.sigma, s.rc, s.box))
         self._systems_arr = arr
         flags = PAMD_FLAG_ONE_CHAIN_PER_LAUNCH if one_chain_per_launch else 0
+        if ho_exact_propagator:
+            flags |= PAMD_FLAG_HO_EXACT_PROPAGATOR
+        if regenerate_flat:
+            flags |= PAMD_FLAG_REGENERATE_FLAT
         self.c = _lib.pamd_problem(self.D, self.beta, self.dt, len(self.systems),
                                    ctypes.cast(arr, ctypes.POINTER(_lib.pamd_system)),
                                    PAMD_FP32 if precision == "fp32" else PAMD_FP64, flags)

@@ -26,6 +26,8 @@ PAMD_LJ = 1
 PAMD_FP32 = 0
 PAMD_FP64 = 1
 PAMD_FLAG_ONE_CHAIN_PER_LAUNCH = 1
+PAMD_FLAG_HO_EXACT_PROPAGATOR = 2
+PAMD_FLAG_REGENERATE_FLAT = 4
 
 #: Every entry point declared in include/pamd.h.
 EXPORTS = (

@@ -14,6 +14,10 @@
 // over the fragment's own steps; each residual belongs to exactly one fragment,
 // so all fragments of all chains are decided in parallel.
 //
+// The harmonic step action is S_t = cS |x_{t+1} - x_t + g x_t|^2 (g, cS from the
+// host: Eq. (3), or the oscillator's exact transition density), and the trial
+// action S0 has its own scale c0 = 1/(4 D dt).
+//
 // fragment_line_kernel (one-line paths, M = 1) and fragment_block_kernel (any
 // M <= 32): one CTA per chain with the chain's path X and the walk W staged in
 // shared memory.  The walks are a segmented prefix sum (warp shuffles along the
@@ -43,7 +47,6 @@ struct FragSys {
     long long off;   // element offset of chain 0
     int T, M;        // steps, elements per slice
     int chain0;      // global index of chain 0
-    double k;        // harmonic constant
 };
 
 // Level and offset of one chain's step (Philox stream 3), or given.
@@ -83,33 +86,33 @@ struct FragGeom {
 };
 
 // Metropolis-Hastings test of fragment f with the fragment sums s = sum r'^2 - r^2
-// and s0 = sum dy^2 - dx^2:  log u < log alpha = (s0 - s) / (4 D dt), with u
-// given as log u or the 53-bit uniform (mant + 1) 2^-53 of Philox stream 5.
-// For FP32 paths the test is first made in FP32 with the top 24 bits of u; only
-// when the two sides lie within a bound of the FP32 errors
-// (|log u - log u24| <= 2^-23/u24, rounding of la and of logf) is it repeated
-// in double.  The decision always equals the double one.
+// and s0 = sum dy^2 - dx^2:  log u < log alpha = s0 c0 - s cS, with u given as
+// log u or the 53-bit uniform (mant + 1) 2^-53 of Philox stream 5.  For FP32
+// paths the test is first made in FP32 with the top 24 bits of u; only when
+// the two sides lie within a bound of the FP32 errors (|log u - log u24| <=
+// 2^-23/u24, rounding of la and of logf) is it repeated in double.  The
+// decision always equals the double one.
 template <typename R>
-__device__ __forceinline__ bool frag_accept(R s, R s0, double c4, float c4f, const double* log_u,
-                                            int fstride, int c, int f, uint64_t seed,
-                                            uint64_t counter)
+__device__ __forceinline__ bool frag_accept(R s, R s0, double cS, float cSf, double c0, float c0f,
+                                            const double* log_u, int fstride, int c, int f,
+                                            uint64_t seed, uint64_t counter)
 {
-    if (log_u) return log_u[(long long)c * fstride + f] < ((double)s0 - (double)s) * c4;
+    if (log_u) return log_u[(long long)c * fstride + f] < (double)s0 * c0 - (double)s * cS;
     const uint4 ctr = make_uint4((uint32_t)f, (uint32_t)c, (uint32_t)counter,
                                  (uint32_t)((counter >> 32) & 0xFFFFu) | (kStreamFragAccept << 16));
     const uint4 w = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
     if (sizeof(R) == 4 && (w.x >> 8) != 0u) {
         const float sh = (float)s, s0h = (float)s0;
-        const float laf = (s0h - sh) * c4f;
+        const float laf = s0h * c0f - sh * cSf;
         const float u24 = (float)((w.x >> 8) + 1u) * 5.9604644775390625e-8f;
         const float lf = logf(u24);
-        const float margin = 1e-5f * (1.0f + (fabsf(sh) + fabsf(s0h)) * c4f + fabsf(lf)) +
+        const float margin = 1e-5f * (1.0f + fabsf(sh) * cSf + fabsf(s0h) * c0f + fabsf(lf)) +
                              2.384185791015625e-7f / u24;  // 2^-22 / u24
         if (fabsf(laf - lf) > margin) return lf < laf;
     }
     const uint64_t mant = (uint64_t)(w.x >> 5) * 67108864ull + (uint64_t)(w.y >> 6);
     const double u = ((double)mant + 1.0) * 1.1102230246251565e-16;
-    return log(u) < ((double)s0 - (double)s) * c4;
+    return log(u) < (double)s0 * c0 - (double)s * cS;
 }
 
 constexpr int kFragMaxThreads = 256;
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kFragMaxThreads)
                           uint64_t counter, const int* __restrict__ levels,
                           const int* __restrict__ offsets, const R* __restrict__ noise,
                           const double* __restrict__ log_u, int fstride, int nfrag_max, R ak, R sig,
-                          double c4, float c4f, int* __restrict__ n_accepted,
+                          double cS, float cSf, double c0, float c0f, int* __restrict__ n_accepted,
                           int* __restrict__ n_proposed)
 {
     extern __shared__ __align__(16) unsigned char frag_smem[];
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(kFragMaxThreads)
         int acc = 0;
         const int fa = G.a(f), fb = G.b(f);
         if (f == G.nfrag - 1 || fb - fa >= 2) {
-            acc = frag_accept<R>(FS[f], FS0[f], c4, c4f, log_u, fstride, c, f, seed, counter);
+            acc = frag_accept<R>(FS[f], FS0[f], cS, cSf, c0, c0f, log_u, fstride, c, f, seed, counter);
             atomicAdd(cnt, 1);
             if (acc) atomicAdd(cnt + 1, 1);
         }
@@ -510,6 +513,7 @@ struct ShiftOut {
     R* traj;          // this system's [chains][n_shift] block of the trajectory
     int n_shift;
     uint64_t counter;
+    double sig;       // width of a regeneration step (0: the line x_T continues)
 };
 
 template <typename R>
@@ -518,7 +522,7 @@ __global__ void __launch_bounds__(kFragMaxThreads)
                          uint64_t counter, const int* __restrict__ levels,
                          const int* __restrict__ offsets, const R* __restrict__ noise,
                          const double* __restrict__ log_u, int fstride, int nfrag_max, R ak, R sig,
-                         double c4, float c4f, int* __restrict__ n_accepted,
+                         double cS, float cSf, double c0, float c0f, int* __restrict__ n_accepted,
                          int* __restrict__ n_proposed, const ShiftOut<R> sh)
 {
     extern __shared__ __align__(16) unsigned char frag_smem[];
@@ -731,7 +735,7 @@ __global__ void __launch_bounds__(kFragMaxThreads)
         const int fa = G.a(f), fb = G.b(f);
         if (f == G.nfrag - 1 || fb - fa >= 2) {
             atomicAdd(cnt, 1);
-            if (frag_accept<R>(FS[f], FS0[f], c4, c4f, log_u, fstride, c, f, seed, counter)) {
+            if (frag_accept<R>(FS[f], FS0[f], cS, cSf, c0, c0f, log_u, fstride, c, f, seed, counter)) {
                 accf[atomicAdd(cnt + 1, 1)] = f;
                 if (sh.out) aflag[f] = 1;
             }
@@ -775,8 +779,9 @@ __global__ void __launch_bounds__(kFragMaxThreads)
     }
     if (tid == nt - 1) {
         R x = final_at(T);
+        const R sr = (R)sh.sig;
         for (int k = 1; k <= ns; ++k) {
-            x = fma_r(sig, Zs[k - 1], x);
+            x = fma_r(sr, Zs[k - 1], x);
             gO[T - ns + k] = x;
         }
     }
@@ -787,8 +792,8 @@ __global__ void __launch_bounds__(128)
     fragment_thread_kernel(R* __restrict__ pos, const FragSys S, int l_min, int l_max, uint64_t seed,
                            uint64_t counter, const int* __restrict__ levels,
                            const int* __restrict__ offsets, const R* __restrict__ noise,
-                           const double* __restrict__ log_u, int fstride, R ak, R sig, double c4,
-                           int* __restrict__ n_accepted, int* __restrict__ n_proposed)
+                           const double* __restrict__ log_u, int fstride, R ak, R sig, double cS,
+                           double c0, int* __restrict__ n_accepted, int* __restrict__ n_proposed)
 {
     const int b_chain = blockIdx.y;
     const int c = S.chain0 + b_chain;
@@ -849,7 +854,9 @@ __global__ void __launch_bounds__(128)
     dS += (double)bS;
     dS0 += (double)bS0;
     atomicAdd(n_proposed + c, 1);
-    if (!frag_accept<double>(dS, dS0, c4, (float)c4, log_u, fstride, c, f, seed, counter)) return;
+    if (!frag_accept<double>(dS, dS0, cS, (float)cS, c0, (float)c0, log_u, fstride, c, f, seed,
+                             counter))
+        return;
     atomicAdd(n_accepted + c, 1);
     for (int m = 0; m < M; ++m) {
         const R xa = X[(long long)fa * M + m], xb = X[(long long)fb * M + m];
@@ -874,11 +881,12 @@ bool fragment_event_fusable(int T, int M, int l_min, int n_shift)
 
 template <typename R>
 cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains, int chain0,
-                               double k, int l_min, int l_max, uint64_t seed, uint64_t counter,
+                               int l_min, int l_max, uint64_t seed, uint64_t counter,
                                const int* levels, const int* offsets, const R* noise,
-                               const double* log_u, int fstride, double a, double sig, double c4,
-                               int* n_accepted, int* n_proposed, cudaStream_t st, R* shift_out,
-                               R* shift_traj, int n_shift, uint64_t shift_counter)
+                               const double* log_u, int fstride, double g, double sig, double cS,
+                               double c0, int* n_accepted, int* n_proposed, cudaStream_t st,
+                               R* shift_out, R* shift_traj, int n_shift, uint64_t shift_counter,
+                               double shift_sig)
 {
     if (n_chains <= 0) return cudaSuccess;
     ShiftOut<R> sh;
@@ -886,13 +894,13 @@ cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains
     sh.traj = shift_traj;
     sh.n_shift = shift_out ? n_shift : 0;
     sh.counter = shift_counter;
+    sh.sig = shift_sig;
     if (shift_out && !fragment_event_fusable<R>(T, M, l_min, n_shift)) return cudaErrorInvalidValue;
     FragSys S;
     S.off = off;
     S.T = T;
     S.M = M;
     S.chain0 = chain0;
-    S.k = k;
     const int nfrag_max = (T >> l_min) + 2;
     const long long E = (long long)(T + 1) * M;
     int threads = (int)std::min<long long>(kFragMaxThreads, ((E + 15) / 16 + 31) / 32 * 32);
@@ -911,7 +919,7 @@ cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains
         if (e != cudaSuccess) return e;
         fragment_line_kernel<R><<<n_chains, lthreads, lsmem, st>>>(
             pos, S, l_min, l_max, seed, counter, levels, offsets, noise, log_u, fstride, nfrag_max,
-            (R)(a * k), (R)sig, c4, (float)c4, n_accepted, n_proposed, sh);
+            (R)g, (R)sig, cS, (float)cS, c0, (float)c0, n_accepted, n_proposed, sh);
         return cudaGetLastError();
     }
     const size_t smem = frag_block_smem<R>(T, M, nfrag_max, threads / 32);
@@ -923,31 +931,31 @@ cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<n_chains, threads, smem, st>>>(pos, S, l_min, l_max, seed, counter, levels, offsets,
-                                              noise, log_u, fstride, nfrag_max, (R)(a * k), (R)sig,
-                                              c4, (float)c4, n_accepted, n_proposed);
+                                              noise, log_u, fstride, nfrag_max, (R)g, (R)sig, cS,
+                                              (float)cS, c0, (float)c0, n_accepted, n_proposed);
         return cudaGetLastError();
     }
     const int tthreads = 128;
     dim3 grid((nfrag_max + tthreads - 1) / tthreads, n_chains);
     fragment_thread_kernel<R><<<grid, tthreads, 0, st>>>(pos, S, l_min, l_max, seed, counter,
                                                          levels, offsets, noise, log_u, fstride,
-                                                         (R)(a * k), (R)sig, c4, n_accepted,
+                                                         (R)g, (R)sig, cS, c0, n_accepted,
                                                          n_proposed);
     return cudaGetLastError();
 }
 
 template bool fragment_event_fusable<float>(int, int, int, int);
 template bool fragment_event_fusable<double>(int, int, int, int);
-template cudaError_t launch_fragment_mc<float>(float*, long long, int, int, int, int, double, int,
-                                               int, uint64_t, uint64_t, const int*, const int*,
+template cudaError_t launch_fragment_mc<float>(float*, long long, int, int, int, int, int, int,
+                                               uint64_t, uint64_t, const int*, const int*,
                                                const float*, const double*, int, double, double,
-                                               double, int*, int*, cudaStream_t, float*, float*, int,
-                                               uint64_t);
-template cudaError_t launch_fragment_mc<double>(double*, long long, int, int, int, int, double, int,
-                                                int, uint64_t, uint64_t, const int*, const int*,
+                                               double, double, int*, int*, cudaStream_t, float*,
+                                               float*, int, uint64_t, double);
+template cudaError_t launch_fragment_mc<double>(double*, long long, int, int, int, int, int, int,
+                                                uint64_t, uint64_t, const int*, const int*,
                                                 const double*, const double*, int, double, double,
-                                                double, int*, int*, cudaStream_t, double*, double*,
-                                                int, uint64_t);
+                                                double, double, int*, int*, cudaStream_t, double*,
+                                                double*, int, uint64_t, double);
 
 // ------------------------------------------------------------------ shift and regenerate
 // Trajectory points x_1..x_{n_shift} of every chain are copied out, the path is

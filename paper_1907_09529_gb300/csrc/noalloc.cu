@@ -139,6 +139,7 @@ extern "C" int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void*
     if (!prob || !prob->systems || prob->n_systems <= 0 || !pos || !S || !grad) return PAMD_ERR_ARG;
     if (prob->precision != PAMD_FP32 && prob->precision != PAMD_FP64) return PAMD_ERR_ARG;
     if (!(prob->D > 0) || !(prob->dt > 0) || !(prob->beta > 0)) return PAMD_ERR_ARG;
+    if (prob->flags & ~PAMD_FLAG_ONE_CHAIN_PER_LAUNCH) return PAMD_ERR_UNSUPPORTED;  // Eq. (3) only
     long long blocks = 0;
     for (int q = 0; q < prob->n_systems; ++q) {
         const pamd_system& s = prob->systems[q];

@@ -135,6 +135,9 @@ std::map<std::string, std::unique_ptr<Plan>> g_plans;
 int check_problem(const pamd_problem* p)
 {
     if (!p || !p->systems || p->n_systems <= 0) return PAMD_ERR_ARG;
+    if (p->flags & ~(PAMD_FLAG_ONE_CHAIN_PER_LAUNCH | PAMD_FLAG_HO_EXACT_PROPAGATOR |
+                     PAMD_FLAG_REGENERATE_FLAT))
+        return PAMD_ERR_ARG;
     if (p->precision != PAMD_FP32 && p->precision != PAMD_FP64) return PAMD_ERR_ARG;
     if (!(p->D > 0) || !(p->dt > 0) || !(p->beta > 0)) return PAMD_ERR_ARG;
     for (int q = 0; q < p->n_systems; ++q) {
@@ -157,6 +160,36 @@ int check_problem(const pamd_problem* p)
         }
     }
     return PAMD_OK;
+}
+
+// The Eq. (3) entry points: the exact-propagator flag belongs to the sampler.
+int check_em_problem(const pamd_problem* p)
+{
+    const int rc = check_problem(p);
+    if (rc) return rc;
+    return (p->flags & PAMD_FLAG_HO_EXACT_PROPAGATOR) ? PAMD_ERR_UNSUPPORTED : PAMD_OK;
+}
+
+// Width of a regeneration step: free-particle steps sqrt(2 D dt) z, or 0 (the
+// path continues as the horizontal line x_T; fma(0, z, x) = x exactly).
+double regen_sigma(const pamd_problem* p)
+{
+    return (p->flags & PAMD_FLAG_REGENERATE_FLAT) ? 0.0 : std::sqrt(2.0 * p->D * p->dt);
+}
+
+// Drift factor g and action scale c of one harmonic system's steps,
+// S_t = c |x_{t+1} - x_t + g x_t|^2: Eq. (3) (g = beta D k dt, c = 1/(4 D dt)) or
+// the exact transition density (g = 1 - phi, c = beta k / (2 (1 - phi^2))).
+void ho_step_constants(const pamd_problem* p, double k, double* g, double* c)
+{
+    if (p->flags & PAMD_FLAG_HO_EXACT_PROPAGATOR) {
+        const double phi = std::exp(-p->beta * p->D * k * p->dt);
+        *g = 1.0 - phi;
+        *c = p->beta * k / (2.0 * (1.0 - phi * phi));
+    } else {
+        *g = p->beta * p->D * p->dt * k;
+        *c = 1.0 / (4.0 * p->D * p->dt);
+    }
 }
 
 std::string plan_key(const pamd_problem* p)
@@ -601,7 +634,7 @@ static int action_common(const pamd_problem* prob, const void* pos, double* S, v
                          bool with_grad, void* stream)
 {
     NvtxRange nvtx_(with_grad ? "pamd_action_grad" : "pamd_action");
-    int rc = check_problem(prob);
+    int rc = check_em_problem(prob);
     if (rc) return rc;
     if (!pos || !S || (with_grad && !grad)) return PAMD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mutex);
@@ -654,7 +687,7 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
                      const double* log_u, int* n_accepted, double* log_alpha, void* stream)
 {
     NvtxRange nvtx_("pamd_path_update");
-    int rc = check_problem(prob);
+    int rc = check_em_problem(prob);
     if (rc) return rc;
     if (!pos || !grad || !S || !(h > 0) || n_updates < 0) return PAMD_ERR_ARG;
     if ((noise || log_u) && n_updates != 1) return PAMD_ERR_ARG;
@@ -768,7 +801,7 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
                          const void* noise, void* stream)
 {
     NvtxRange nvtx_("pamd_euler_reference");
-    int rc = check_problem(prob);
+    int rc = check_em_problem(prob);
     if (rc) return rc;
     if (!pos) return PAMD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mutex);
@@ -846,25 +879,26 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
         if (ptr && is_host_ptr(ptr)) return PAMD_ERR_ARG;  // device buffers only
     const int fstride = (Tmax >> l_min) + 2;
     cudaStream_t st = (cudaStream_t)stream;
-    const double a = prob->beta * prob->D * prob->dt, sig = std::sqrt(2.0 * prob->D * prob->dt);
-    const double c4 = 1.0 / (4.0 * prob->D * prob->dt);
+    const double sig = std::sqrt(2.0 * prob->D * prob->dt), c0 = 1.0 / (4.0 * prob->D * prob->dt);
     for (int u = 0; u < n_steps; ++u) {
         int chain0 = 0;
         for (int q = 0; q < prob->n_systems; ++q) {
             const pamd_system& s = prob->systems[q];
             const int M = s.dim * s.n_particles;
+            double g, cS;
+            ho_step_constants(prob, s.pot.k, &g, &cS);
             if (prob->precision == PAMD_FP64)
                 PAMD_CUDA_TRY(launch_fragment_mc<double>((double*)pos, s.pos_offset, s.n_steps, M,
-                                                         s.n_chains, chain0, s.pot.k, l_min, l_max,
-                                                         seed, counter + u, levels, offsets,
-                                                         (const double*)noise, log_u, fstride, a,
-                                                         sig, c4, n_accepted, n_proposed, st));
+                                                         s.n_chains, chain0, l_min, l_max, seed,
+                                                         counter + u, levels, offsets,
+                                                         (const double*)noise, log_u, fstride, g,
+                                                         sig, cS, c0, n_accepted, n_proposed, st));
             else
                 PAMD_CUDA_TRY(launch_fragment_mc<float>((float*)pos, s.pos_offset, s.n_steps, M,
-                                                        s.n_chains, chain0, s.pot.k, l_min, l_max,
-                                                        seed, counter + u, levels, offsets,
-                                                        (const float*)noise, log_u, fstride, a, sig,
-                                                        c4, n_accepted, n_proposed, st));
+                                                        s.n_chains, chain0, l_min, l_max, seed,
+                                                        counter + u, levels, offsets,
+                                                        (const float*)noise, log_u, fstride, g, sig,
+                                                        cS, c0, n_accepted, n_proposed, st));
             chain0 += s.n_chains;
         }
     }
@@ -893,8 +927,7 @@ int pamd_event(const pamd_problem* prob, void* pos, void* pos_out, int n_sample,
         if (is_host_ptr(ptr)) return PAMD_ERR_ARG;
     const int fstride = (Tmax >> l_min) + 2;
     cudaStream_t st = (cudaStream_t)stream;
-    const double a = prob->beta * prob->D * prob->dt, sig = std::sqrt(2.0 * prob->D * prob->dt);
-    const double c4 = 1.0 / (4.0 * prob->D * prob->dt);
+    const double sig = std::sqrt(2.0 * prob->D * prob->dt), c0 = 1.0 / (4.0 * prob->D * prob->dt);
     const bool fp64 = prob->precision == PAMD_FP64;
     long long traj_off = 0;
     int chain0 = 0;
@@ -903,31 +936,33 @@ int pamd_event(const pamd_problem* prob, void* pos, void* pos_out, int n_sample,
         const int M = s.dim * s.n_particles, T = s.n_steps;
         const bool fuse = fp64 ? fragment_event_fusable<double>(T, M, l_min, n_shift)
                                : fragment_event_fusable<float>(T, M, l_min, n_shift);
+        double g, cS;
+        ho_step_constants(prob, s.pot.k, &g, &cS);
         for (int u = 0; u < n_sample; ++u) {
             const uint64_t ctr = event * (uint64_t)n_sample + (uint64_t)u;
             const bool last = fuse && u == n_sample - 1;
             if (fp64)
                 PAMD_CUDA_TRY(launch_fragment_mc<double>(
-                    (double*)pos, s.pos_offset, T, M, s.n_chains, chain0, s.pot.k, l_min, l_max, seed,
-                    ctr, nullptr, nullptr, nullptr, nullptr, fstride, a, sig, c4, n_accepted,
+                    (double*)pos, s.pos_offset, T, M, s.n_chains, chain0, l_min, l_max, seed, ctr,
+                    nullptr, nullptr, nullptr, nullptr, fstride, g, sig, cS, c0, n_accepted,
                     n_proposed, st, last ? (double*)pos_out : nullptr,
-                    last ? (double*)traj + traj_off : nullptr, n_shift, event));
+                    last ? (double*)traj + traj_off : nullptr, n_shift, event, regen_sigma(prob)));
             else
                 PAMD_CUDA_TRY(launch_fragment_mc<float>(
-                    (float*)pos, s.pos_offset, T, M, s.n_chains, chain0, s.pot.k, l_min, l_max, seed,
-                    ctr, nullptr, nullptr, nullptr, nullptr, fstride, a, sig, c4, n_accepted,
+                    (float*)pos, s.pos_offset, T, M, s.n_chains, chain0, l_min, l_max, seed, ctr,
+                    nullptr, nullptr, nullptr, nullptr, fstride, g, sig, cS, c0, n_accepted,
                     n_proposed, st, last ? (float*)pos_out : nullptr,
-                    last ? (float*)traj + traj_off : nullptr, n_shift, event));
+                    last ? (float*)traj + traj_off : nullptr, n_shift, event, regen_sigma(prob)));
         }
         if (!fuse) {
             if (fp64)
                 PAMD_CUDA_TRY(launch_shift_regenerate<double>(
                     (const double*)pos, (double*)pos_out, (double*)traj, s.pos_offset, traj_off, T, M,
-                    n_shift, s.n_chains, chain0, sig, seed, event, nullptr, st));
+                    n_shift, s.n_chains, chain0, regen_sigma(prob), seed, event, nullptr, st));
             else
                 PAMD_CUDA_TRY(launch_shift_regenerate<float>(
                     (const float*)pos, (float*)pos_out, (float*)traj, s.pos_offset, traj_off, T, M,
-                    n_shift, s.n_chains, chain0, sig, seed, event, nullptr, st));
+                    n_shift, s.n_chains, chain0, regen_sigma(prob), seed, event, nullptr, st));
         }
         traj_off += (long long)s.n_chains * n_shift * M;
         chain0 += s.n_chains;
@@ -948,7 +983,7 @@ int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_o
     for (const void* ptr : {pos, (const void*)pos_out, (const void*)traj, noise})
         if (ptr && is_host_ptr(ptr)) return PAMD_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const double sig = std::sqrt(2.0 * prob->D * prob->dt);
+    const double sig = regen_sigma(prob);
     long long traj_off = 0;
     int chain0 = 0;
     for (int q = 0; q < prob->n_systems; ++q) {

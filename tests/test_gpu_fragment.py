@@ -121,6 +121,27 @@ def test_shift_regenerate_matches_oracle(pamd):
         assert np.array_equal(traj[b], tr)
 
 
+def test_flat_regeneration_matches_oracle(pamd):
+    """PAMD_FLAG_REGENERATE_FLAT: the regrown nose is the line x_T, i.e. the
+    oracle's regeneration with zero noise, exactly."""
+    from paper_1907_09529_gb300 import integrator
+    B, T, d, n_shift = 3, 40, 2, 9
+    rng = inputs.rng(303)
+    prob = pamd.Problem([pamd.System("harmonic", 1, d, T, B)], 0.7, 1.0, 0.2, precision="fp64",
+                        regenerate_flat=True)
+    paths = rng.standard_normal((B, T + 1, d, 1))
+    buf = prob.empty("cuda")
+    prob.view(buf, 0).copy_(torch.from_numpy(paths))
+    out = prob.empty("cuda")
+    traj = integrator.shift_regenerate(prob, buf, out, n_shift, seed=5, counter=1)
+    torch.cuda.synchronize()
+    got = prob.view(out, 0).cpu().numpy()
+    for b in range(B):
+        o, tr = oracle.shift_regenerate(paths[b], n_shift, np.zeros((n_shift, d, 1)), 0.7, 0.2)
+        assert np.array_equal(got[b], o)
+    assert np.array_equal(traj.view(B, n_shift, d, 1).cpu().numpy(), paths[:, 1:n_shift + 1])
+
+
 def test_pamd_loop_reproduces_the_euler_chain_statistics(pamd):
     """The integrated trajectories of 4096 PAMD chains (N_path = 16, N_shift = 1,
     N_sample = 16, levels 1..3, dt = 0.1) have the stationary variance
@@ -222,21 +243,26 @@ def test_fragment_mc_full_size_sampled_chains(pamd):
     assert float(acc.sum()) > 0
 
 
-@pytest.mark.parametrize("precision,d,T,n_sample,n_shift,l_min,l_max", [
-    ("fp32", 1, 4096, 1, 64, 4, 8),    # fused epilogue (one-line paths)
-    ("fp32", 1, 256, 3, 16, 2, 5),
-    ("fp64", 1, 1024, 2, 7, 3, 6),
-    ("fp32", 3, 512, 2, 10, 2, 4),     # several lines: separate shift kernels
-    ("fp64", 1, 40000, 1, 33, 5, 9),   # too large for one CTA: separate kernels
+@pytest.mark.parametrize("precision,d,T,n_sample,n_shift,l_min,l_max,opts", [
+    ("fp32", 1, 4096, 1, 64, 4, 8, ""),    # fused epilogue (one-line paths)
+    ("fp32", 1, 256, 3, 16, 2, 5, ""),
+    ("fp64", 1, 1024, 2, 7, 3, 6, ""),
+    ("fp32", 3, 512, 2, 10, 2, 4, ""),     # several lines: separate shift kernels
+    ("fp64", 1, 40000, 1, 33, 5, 9, ""),   # too large for one CTA: separate kernels
+    ("fp32", 1, 4096, 1, 64, 4, 8, "exact,flat"),
+    ("fp32", 3, 512, 2, 10, 2, 4, "exact,flat"),
+    ("fp64", 1, 1024, 2, 7, 3, 6, "flat"),
 ])
-def test_event_matches_separate_calls(pamd, precision, d, T, n_sample, n_shift, l_min, l_max):
+def test_event_matches_separate_calls(pamd, precision, d, T, n_sample, n_shift, l_min, l_max,
+                                      opts):
     """pamd_event equals n_sample pamd_fragment_mc steps followed by
     pamd_shift_regenerate, bit for bit, for paths, trajectory and counts."""
     from paper_1907_09529_gb300 import integrator
     B, seed, ev = 5, 97531, 3
     prob = pamd.Problem([pamd.System("harmonic", 1, d, T, B),
                          pamd.System("harmonic", 1, d, T // 2, 2)], 1.0, 1.0, 0.3,
-                        precision=precision)
+                        precision=precision, ho_exact_propagator="exact" in opts,
+                        regenerate_flat="flat" in opts)
     g = torch.Generator(device="cuda")
     g.manual_seed(3)
     a = prob.empty("cuda")
