@@ -304,7 +304,7 @@ def run_sampler(args, w, pamd, prob, dev, rank, world):
             o = int(rng.integers(0, 1 << l))
             z = rng.standard_normal(x.shape)
             lu = np.log(rng.random(oracle.n_fragments(T, l, o)))
-            oracle.fragment_step(pot, x, l, o, z, lu, w.D, w.beta, w.dt)
+            oracle.fragment_step(pot, x, l, o, z, lu, w.D, w.beta, w.dt, exact_ho=True)
             n += 1
         dtm = time.perf_counter() - t0
         cpu = {"value": n * T / dtm, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -316,7 +316,8 @@ def run_sampler(args, w, pamd, prob, dev, rank, world):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
                "config": {"workload": (f"ho_pamd: 1D harmonic oscillator, PAMD loop (Fig. 2) with "
-                                       f"the multilevel sampler (Sec. III), dt={w.dt}, "
+                                       f"the multilevel sampler (Sec. III), exact propagator, "
+                                       f"straight-line regeneration, dt={w.dt}, "
                                        f"N_path={spec.T}, N_sample={n_sample}, N_shift={n_shift}, "
                                        f"levels {l_min}..{l_max}, {spec.n_chains} chains"),
                           "units": "MD force evaluations of the sampler (N_sample * N_path per "
@@ -379,7 +380,13 @@ def main():
             systems.append(pamd.System("lj", s.N, s.d, s.T, s.n_chains, box=s.box, rc=s.rc_eff))
         else:
             systems.append(pamd.System("harmonic", s.N, s.d, s.T, s.n_chains, k=s.k))
-    prob = pamd.Problem(systems, w.D, w.beta, w.dt, "fp32")
+    if w.name == "ho_pamd":
+        # the paper's Simulation 3 as validated: exact oscillator propagator,
+        # straight-line regeneration
+        prob = pamd.Problem(systems, w.D, w.beta, w.dt, "fp32", ho_exact_propagator=True,
+                            regenerate_flat=True)
+    else:
+        prob = pamd.Problem(systems, w.D, w.beta, w.dt, "fp32")
     stream = torch.cuda.current_stream(dev)
     if w.name == "ho_pamd":
         run_sampler(args, w, pamd, prob, dev, rank, world)
