@@ -140,7 +140,7 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "lj_action_kernel": ("lj_kernels.cu", "pamd_internal.cuh"),
     "ho_vec_kernel": ("ho_kernels.cu", "pamd_internal.cuh"),
-    "fragment_line_kernel": ("fragment_kernels.cu", "pamd_internal.cuh"),
+    "fragment_line_kernel": ("fragment_kernels.cu", "fragment.cuh", "pamd_internal.cuh"),
 }
 
 

@@ -39,7 +39,7 @@
 // the accept test is decided in double whenever the FP32 margin cannot.
 #include <algorithm>
 
-#include "pamd_internal.cuh"
+#include "fragment.cuh"
 
 namespace pamd {
 

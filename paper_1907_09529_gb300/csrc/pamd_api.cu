@@ -18,6 +18,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "pamd_internal.cuh"
+#include "fragment.cuh"
 
 using namespace pamd;
 

@@ -301,33 +301,6 @@ cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter,
 
 cudaError_t launch_philox(uint4 ctr, uint2 key, long long n, uint32_t* out, cudaStream_t st);
 
-// Shift every chain of one system by n_shift steps into `out`, emit the
-// trajectory points, regrow the nose with free-particle steps.
-template <typename R>
-cudaError_t launch_shift_regenerate(const R* pos, R* out, R* traj, long long off, long long traj_off,
-                                    int T, int M, int n_shift, int n_chains, int chain0, double sig,
-                                    uint64_t seed, uint64_t counter, const R* noise, cudaStream_t st);
-
-// One multilevel sliding-and-sampling MC step of every chain of one harmonic
-// system (free-particle trials).
-// Largest shared-memory footprint of the one-CTA-per-chain fragment kernel;
-// larger chains take the one-thread-per-fragment kernel.
-constexpr size_t kFragBlockSmemMax = 192 * 1024;
-
-template <typename R>
-bool fragment_event_fusable(int T, int M, int l_min, int n_shift);
-// shift_out != nullptr: fuse the shift epilogue of a shifting event (one-line
-// systems only, see fragment_event_fusable)
-// g, cS: drift factor and action scale of a step, S_t = cS |x_{t+1} - x_t + g x_t|^2;
-// c0: scale of the free-particle trial action.
-template <typename R>
-cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains, int chain0,
-                               int l_min, int l_max, uint64_t seed, uint64_t counter,
-                               const int* levels, const int* offsets, const R* noise,
-                               const double* log_u, int fstride, double g, double sig, double cS,
-                               double c0, int* n_accepted, int* n_proposed, cudaStream_t st,
-                               R* shift_out = nullptr, R* shift_traj = nullptr, int n_shift = 0,
-                               uint64_t shift_counter = 0, double shift_sig = 0.0);
 cudaError_t launch_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, uint32_t chain,
                            long long e0, long long n, float* out, cudaStream_t st);
 
