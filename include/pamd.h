@@ -247,7 +247,8 @@ int pamd_event(const pamd_problem* prob, void* pos, void* pos_out, int n_sample,
  * the kernels' rule (dx = xi - xj; k = fmaf(dx, 1/L, 1.5*2^23) - 1.5*2^23;
  * dx = fmaf(-L, k, dx); r2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx)); in iff
  * r2 <= rc*rc), with L, 1/L, rc*rc rounded to float.  PAMD_FP32 only.
- *   counts : long long[sum over LJ chains of (T+1)], chain-major, written. */
+ *   counts : long long[sum over LJ chains of (T+1)], chain-major, written.
+ * A Lennard-Jones system with more than 65535 chains: PAMD_ERR_UNSUPPORTED. */
 int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* counts,
                         void* stream);
 

@@ -935,13 +935,22 @@ cudaError_t launch_fragment_mc(R* pos, long long off, int T, int M, int n_chains
                                               (float)cS, c0, (float)c0, n_accepted, n_proposed);
         return cudaGetLastError();
     }
+    // grid.y holds at most 65535 chains: launch in batches (chain0 and the offset advance)
     const int tthreads = 128;
-    dim3 grid((nfrag_max + tthreads - 1) / tthreads, n_chains);
-    fragment_thread_kernel<R><<<grid, tthreads, 0, st>>>(pos, S, l_min, l_max, seed, counter,
-                                                         levels, offsets, noise, log_u, fstride,
-                                                         (R)g, (R)sig, cS, c0, n_accepted,
-                                                         n_proposed);
-    return cudaGetLastError();
+    for (int b0 = 0; b0 < n_chains; b0 += 65535) {
+        const int nb = std::min(65535, n_chains - b0);
+        FragSys Sb = S;
+        Sb.off = off + (long long)b0 * (long long)(T + 1) * M;
+        Sb.chain0 = chain0 + b0;
+        dim3 grid((nfrag_max + tthreads - 1) / tthreads, nb);
+        fragment_thread_kernel<R><<<grid, tthreads, 0, st>>>(pos, Sb, l_min, l_max, seed, counter,
+                                                             levels, offsets, noise, log_u, fstride,
+                                                             (R)g, (R)sig, cS, c0, n_accepted,
+                                                             n_proposed);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template bool fragment_event_fusable<float>(int, int, int, int);

@@ -1011,6 +1011,9 @@ int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* co
     if (rc) return rc;
     if (!pos || !counts || prob->precision != PAMD_FP32) return PAMD_ERR_ARG;
     if (is_host_ptr(pos) || is_host_ptr(counts)) return PAMD_ERR_ARG;
+    for (int q = 0; q < prob->n_systems; ++q)  // one grid row per chain
+        if (prob->systems[q].pot.kind == PAMD_LJ && prob->systems[q].n_chains > 65535)
+            return PAMD_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     long long out_off = 0;
     for (int q = 0; q < prob->n_systems; ++q) {
