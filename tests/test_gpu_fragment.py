@@ -288,3 +288,38 @@ def test_event_matches_separate_calls(pamd, precision, d, T, n_sample, n_shift, 
     assert torch.equal(traj1, traj2)
     assert torch.equal(acc1, acc2) and torch.equal(prop1, prop2)
     assert int(prop1.sum()) > 0
+
+
+def test_fallback_kernel_beyond_one_grid_of_chains(pamd):
+    """33 elements per slice (11 particles in 3D) take the thread-per-fragment
+    kernel, which launches at most 65535 chains at a time: chains on both sides
+    of that boundary match the oracle fed the same Philox draws."""
+    B, T, N, l_min, l_max, seed, counter = 70000, 16, 11, 2, 3, 4242, 5
+    prob = pamd.Problem([pamd.System("harmonic", N, 3, T, B, k=0.8)], 1.0, 1.0, 0.05,
+                        precision="fp64")
+    buf = prob.empty("cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(9)
+    prob.view(buf, 0).copy_(torch.randn(prob.view(buf, 0).shape, generator=g, device="cuda",
+                                        dtype=torch.float64))
+    before = prob.view(buf, 0)
+    picks = [0, 1, 65534, 65535, 65536, 69999]
+    start = {c: before[c].cpu().numpy().copy() for c in picks}
+    acc, prop = pamd.fragment_mc(prob, buf, l_min, l_max, 1, seed=seed, counter=counter)
+    torch.cuda.synchronize()
+    pot = oracle.harmonic(0.8)
+    M = 3 * N
+    for c in picks:
+        wc = oracle.philox([0, c, counter, 3 << 16], [seed & 0xFFFFFFFF, seed >> 32])
+        l = l_min + int(wc[0]) % (l_max - l_min + 1)
+        o = int(wc[1]) % (1 << l)
+        nf = oracle.n_fragments(T, l, o)
+        z = oracle.normals(seed, counter, 4, c, (T + 1) * M).astype(np.float32).astype(np.float64)
+        lu = np.array([_philox_log_u(seed, counter, c, f) for f in range(nf)])
+        x = start[c].copy()
+        _, na, npr = oracle.fragment_step(pot, x, l, o, z.reshape(T + 1, 3, N), lu, 1.0, 1.0, 0.05)
+        assert (int(acc[c]), int(prop[c])) == (na, npr), c
+        # the kernel's Philox normals are FP32 (Box-Muller in single precision), the
+        # oracle's are FP64 rounded to FP32: they agree to about an ulp
+        got = prob.view(buf, 0)[c].cpu().numpy()
+        assert np.abs(got - x).max() <= 2e-5 * max(1.0, np.abs(x).max()), c
