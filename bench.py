@@ -167,9 +167,11 @@ def profiled_traffic(config, kernel):
 
 
 # ------------------------------------------------------------------ CPU oracle leg
-def oracle_sample(w, budget_s=12.0):
+def oracle_sample(w, budget_s=12.0, single_core=False):
     """Time the CPU oracle's action+gradient on a bounded sample of the workload:
-    one chain of the (first) system, slices grown until ~budget_s of CPU work."""
+    one chain of the (first) system, slices grown until ~budget_s of CPU work.
+    single_core: also time the same oracle on one thread (bit-identical results)
+    on a proportionally shorter sample."""
     import oracle
     import pamd_inputs as inputs
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -180,7 +182,7 @@ def oracle_sample(w, budget_s=12.0):
            else oracle.harmonic(spec.k))
     nth = oracle.max_threads()
 
-    def run(T):
+    def run(T, threads=None):
         T = min(T, spec.T)
         s1 = inputs.SystemSpec(spec.kind, spec.N, spec.d, T, 1)
         if spec.kind == "lj":
@@ -190,7 +192,7 @@ def oracle_sample(w, budget_s=12.0):
         else:
             path = inputs.gaussian_path(3, 1, T, spec.d, spec.N, 1.0)[0]
         t0 = time.perf_counter()
-        oracle.action_grad(pot, path, w.D, w.beta, w.dt, nthreads=nth)
+        oracle.action_grad(pot, path, w.D, w.beta, w.dt, nthreads=threads or nth)
         return T, time.perf_counter() - t0
 
     T, dtm = run(8 if spec.kind == "lj" else 4096)
@@ -204,9 +206,18 @@ def oracle_sample(w, budget_s=12.0):
         total += run(T)[1]
         reps += 1
     units = spec.N * T * reps
-    return {"value": units / total, "unit": UNIT, "cores": nth, "kind": "oracle",
-            "sample": f"{reps} chain(s) of {spec.kind} N={spec.N}, {T} of {spec.T} steps each, "
-                      f"action+gradient ({total:.1f} s, OpenMP over slices)"}
+    res = {"value": units / total, "unit": UNIT, "cores": nth, "kind": "oracle",
+           "sample": f"{reps} chain(s) of {spec.kind} N={spec.N}, {T} of {spec.T} steps each, "
+                     f"action+gradient ({total:.1f} s, OpenMP over slices)"}
+    if single_core:
+        T1, d1 = run(max(2, T // max(1, nth)), threads=1)
+        r1 = 1
+        while d1 < budget_s / 4 and r1 < 64:
+            d1 += run(T1, threads=1)[1]
+            r1 += 1
+        res["single_core"] = {"value": spec.N * T1 * r1 / d1, "unit": UNIT, "cores": 1,
+                              "sample": f"{r1} chain(s), {T1} steps each ({d1:.1f} s, one thread)"}
+    return res
 
 
 def run_reference(args, w):
@@ -557,7 +568,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(w)
+        cpu = oracle_sample(w, single_core=True)
 
     if rank == 0:
         out = {
