@@ -421,7 +421,7 @@ def main():
     tuned = None
     if any(s.kind == "lj" for s in w.systems) and not args.no_autotune and not args.only_kernel:
         from paper_1907_09529_gb300 import autotune as at
-        shapes = list(at.candidates(tiles=(8, 16, 32, 64), skins=(0.25, 0.3, 0.35)))
+        shapes = list(at.candidates(tiles=(16, 32, 64, 128), skins=(0.3, 0.35, 0.4, 0.45)))
         best, timings = at.autotune(prob, pos, shapes, reps=2, cache=None)
         tuned = {"tile_steps": best[0], "skin": best[3],
                  "ms_per_call": round(timings[json.dumps(best)], 4),

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpamd.so")
-SOURCES = ["pamd_api.cu", "ho_kernels.cu", "lj_kernels.cu", "update_kernels.cu", "noalloc.cu",
+SOURCES = ["pamd_api.cu", "ho_kernels.cu", "lj_kernels.cu", "lj_paired.cu", "update_kernels.cu", "noalloc.cu",
            "fragment_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -1,0 +1,497 @@
+// lj_paired.cu -- single-precision Lennard-Jones path action and adjoint with two
+// consecutive steps per thread.
+//
+// The forces of different time slices are independent (Sec. II.B), and along a
+// Brownian path a particle moves ~sqrt(2 D dt) per step, so the neighbours of
+// particle i are the same at steps t and t+1.  This kernel therefore evaluates
+// every pair (i, j) at both steps at once: positions of the two slices sit side
+// by side in shared memory, and every floating-point operation of the pair
+// geometry, the force and the Hessian-vector product is one packed f32x2
+// instruction acting on (step t, step t+1).  Each half of a packed operation is
+// an IEEE single-precision operation, so the result of a step does not depend on
+// the step it is paired with.
+//
+// Formulas (paper Eqs. (3), (11); the cut-and-force-shifted pair potential,
+// u = 4 eps [(s/r)^12 - (s/r)^6], ir2 = 1/r^2, ir6 = ir2^3, w = 24 eps s^6 ir6 ir2):
+//   fs    = -U'(r)/r = w (2 s^6 ir6 - 1) + u'(rc)/r
+//   Bc    = (U''(r) - U'(r)/r)/r^2 = [w (26 s^6 ir6 - 7) + fs] ir2
+//   F_i   = sum_j fs r_ij,                          r_ij = x_i - x_j (minimum image)
+//   r_t   = x_{t+1} - x_t - a F(x_t),               a = beta D dt
+//   (Hv)_i = sum_j [ -fs v_ij + Bc (r_ij . v_ij) r_ij ],   v_ij = v_i - v_j
+//   g_t   = [r_{t-1} - r_t + a H(x_t) r_t] / (2 D dt),  r_{-1} = r_T = 0
+//   S     = sum_t |r_t|^2 / (4 D dt)   (per-item partial sums in FP64)
+// A pair outside the cutoff gets r^2 = +inf, which makes every coefficient an
+// exact zero (rsqrt(+inf) = +0).
+//
+// Work decomposition: a persistent grid pulls (system, chain, tile of steps)
+// items from an atomic queue.  Within an item the steps are walked in pairs
+// (a, a+1).  An item that does not start at step 0 begins with the pair
+// (t0-1, t0), whose first half only supplies the residual r_{t0-1}.
+//
+// Neighbour lists.  A Verlet list of radius rc + skin, built at the first slice
+// of a pair, is used while every particle stays within skin/2 of where it was at
+// the build; if one step breaks that (a path far from Brownian), the pair scans
+// all candidates.  Candidates are visited in increasing j in every case, so each
+// force and Hessian sum runs over the in-cutoff pairs in one fixed order whatever
+// the tiling, skin or list capacity, and the results are bitwise independent of
+// them.
+#include "pamd_internal.cuh"
+
+namespace pamd {
+
+namespace {
+
+// ------------------------------------------------------------------ packed f32x2 arithmetic
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b with one rounding: b * (-1) + a is exact before rounding.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, pk(-1.0f), a); }
+
+__device__ __forceinline__ float rsqrt_approx(float v)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// ------------------------------------------------------------------ shared-memory layout
+// For a block of up to NMAX particles (NMAX = the kernel's maximum block size):
+//   [0, 16 NMAX)        xy[j]  = {x_a, x_b, y_a, y_b} of the positions
+//   [16 NMAX, 32 NMAX)  rxy[j] = the same for the residuals
+//   [32 NMAX, 40 NMAX)  z[j]   = {z_a, z_b} of the positions
+//   [40 NMAX, 48 NMAX)  rz[j]  = the same for the residuals
+//   [48 NMAX, ...)      neighbour lists, two uint16 entries per 32-bit word
+// Two arrays per quantity (16- and 8-byte strides) let a gather of random
+// particles spread over all banks.  A list entry is the byte offset 8 j, so
+// every array is addressed from it with a constant displacement.
+template <int NMAX>
+struct Smem {
+    unsigned char* base;
+    __device__ float4& xy(int o8) const { return *reinterpret_cast<float4*>(base + 2 * o8); }
+    __device__ float4& rxy(int o8) const
+    {
+        return *reinterpret_cast<float4*>(base + 16 * NMAX + 2 * o8);
+    }
+    __device__ float2& z(int o8) const { return *reinterpret_cast<float2*>(base + 32 * NMAX + o8); }
+    __device__ float2& rz(int o8) const { return *reinterpret_cast<float2*>(base + 40 * NMAX + o8); }
+    __device__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 48 * NMAX); }
+};
+
+// Packed constants of one system (built per item from the per-system table).
+struct K2 {
+    float2 nL, iL, mag, nmag, c1, c2, c3, duc, m1, m7;
+    float rc2, rl2, hs2, a, ginv;
+    __device__ explicit K2(const LJK<float>& k)
+    {
+        nL = pk(-k.L);
+        iL = pk(k.iL);
+        mag = pk(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
+        nmag = pk(-12582912.0f);
+        c1 = pk(k.c1);
+        c2 = pk(k.c2);
+        c3 = pk(k.c3);
+        duc = pk(k.duc);
+        m1 = pk(-1.0f);
+        m7 = pk(-7.0f);
+        rc2 = k.rc2;
+        rl2 = k.rl2;
+        hs2 = k.hs2;
+        a = k.a;
+        ginv = k.ginv;
+    }
+};
+
+// Pair vector and r^2 of (step a, step b) by the single-precision minimum-image
+// rule  d = x_i - x_j;  d = fma(-L, round(d * (1/L)), d);  r2 = fma(dz,dz,fma(dy,dy,dx*dx)),
+// with r^2 = +inf for a half outside the cutoff.
+__device__ __forceinline__ float2 pair_geom(float2 xi, float2 yi, float2 zi, float4 pxy, float2 pz,
+                                            const K2& k, float2& dx, float2& dy, float2& dz)
+{
+    dx = sub2(xi, pk(pxy.x, pxy.y));
+    dy = sub2(yi, pk(pxy.z, pxy.w));
+    dz = sub2(zi, pz);
+    dx = fma2(k.nL, add2(fma2(dx, k.iL, k.mag), k.nmag), dx);
+    dy = fma2(k.nL, add2(fma2(dy, k.iL, k.mag), k.nmag), dy);
+    dz = fma2(k.nL, add2(fma2(dz, k.iL, k.mag), k.nmag), dz);
+    float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    const float inf = __int_as_float(0x7f800000);
+    r2.x = r2.x <= k.rc2 ? r2.x : inf;
+    r2.y = r2.y <= k.rc2 ? r2.y : inf;
+    return r2;
+}
+
+// -U'(r)/r from r^2, with w = ir2 u and ir6 for the Hessian coefficient.
+__device__ __forceinline__ float2 pair_fs(float2 r2, const K2& k, float2& w, float2& ir2,
+                                          float2& ir6)
+{
+    const float2 ri = pk(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    ir2 = mul2(ri, ri);
+    ir6 = mul2(mul2(ir2, ir2), ir2);
+    w = mul2(ir2, mul2(k.c1, ir6));
+    return fma2(w, fma2(k.c2, ir6, k.m1), mul2(k.duc, ri));
+}
+
+// The particle a thread works for, its list, and the candidate loop.
+template <int NMAX>
+struct PairList {
+    int N, NT, tid, i, q, tpp, cap, cnt;
+    bool active, ovf;
+    uint32_t* nbr;
+    float xr, yr, zr;
+
+    __device__ void init(int n, int tpp_, int lg, int cap_, uint32_t* list)
+    {
+        N = n;
+        NT = blockDim.x;
+        tid = threadIdx.x;
+        tpp = tpp_;
+        i = tid >> lg;
+        q = tid & (tpp_ - 1);
+        active = i < n;
+        cap = cap_ & ~1;
+        nbr = list;
+        cnt = 0;
+        ovf = false;
+    }
+
+    // Entry c of this thread is half (c & 1) of word (c >> 1) * NT + tid.
+    __device__ __forceinline__ void put(int c, int o8) const
+    {
+        reinterpret_cast<uint16_t*>(nbr + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
+    }
+
+    // Verlet list at slice a: candidates j = q (mod tpp), two per packed operation.
+    __device__ void build(const Smem<NMAX>& P, const K2& k)
+    {
+        cnt = 0;
+        ovf = false;
+        if (!active) return;
+        const int oi = 8 * i;
+        xr = P.xy(oi).x;
+        yr = P.xy(oi).z;
+        zr = P.z(oi).x;
+        const float2 xi = pk(xr), yi = pk(yr), zi = pk(zr);
+        int c = 0;
+        for (int j = q; j < N; j += 2 * tpp) {
+            const int j2 = j + tpp;
+            const int j2c = j2 < N ? j2 : j;
+            const float4 A = P.xy(8 * j), B = P.xy(8 * j2c);
+            float2 dx = sub2(xi, pk(A.x, B.x));
+            float2 dy = sub2(yi, pk(A.z, B.z));
+            float2 dz = sub2(zi, pk(P.z(8 * j).x, P.z(8 * j2c).x));
+            dx = fma2(k.nL, add2(fma2(dx, k.iL, k.mag), k.nmag), dx);
+            dy = fma2(k.nL, add2(fma2(dy, k.iL, k.mag), k.nmag), dy);
+            dz = fma2(k.nL, add2(fma2(dz, k.iL, k.mag), k.nmag), dz);
+            const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+            if (j != i && r2.x <= k.rl2) {
+                if (c < cap) put(c, 8 * j);
+                ++c;
+            }
+            if (j2 < N && j2 != i && r2.y <= k.rl2) {
+                if (c < cap) put(c, 8 * j2);
+                ++c;
+            }
+        }
+        cnt = c;
+        ovf = c > cap;
+    }
+
+    // Has particle i left the skin/2 ball around its build position at slice a
+    // (first) or b (second)?
+    __device__ void moved(const Smem<NMAX>& P, const K2& k, bool& ma, bool& mb) const
+    {
+        ma = mb = false;
+        if (!active) return;
+        const float4 pxy = P.xy(8 * i);
+        const float2 pz = P.z(8 * i);
+        const float ax = pxy.x - xr, ay = pxy.z - yr, az = pz.x - zr;
+        const float bx = pxy.y - xr, by = pxy.w - yr, bz = pz.y - zr;
+        ma = ax * ax + ay * ay + az * az > k.hs2;
+        mb = bx * bx + by * by + bz * bz > k.hs2;
+    }
+
+    // Calls f(8 j) for the candidates j of particle i, in increasing j.
+    template <typename F>
+    __device__ __forceinline__ void for_each_candidate(bool scan_all, F&& f) const
+    {
+        if (!active) return;
+        if (!ovf && !scan_all) {
+            const uint32_t* w = nbr + tid;
+            int m = 0;
+            for (; m + 1 < cnt; m += 2, w += NT) {
+                const uint32_t v = *w;
+                f((int)(v & 0xFFFFu));
+                f((int)(v >> 16));
+            }
+            if (m < cnt) f((int)(*w & 0xFFFFu));
+        } else {
+            for (int j = q; j < N; j += tpp)
+                if (j != i) f(8 * j);
+        }
+    }
+
+    __device__ __forceinline__ void group_sum(float2& x, float2& y, float2& z) const
+    {
+        for (int o = tpp >> 1; o > 0; o >>= 1) {
+            x = add2(x, pk(__shfl_xor_sync(0xffffffffu, x.x, o), __shfl_xor_sync(0xffffffffu, x.y, o)));
+            y = add2(y, pk(__shfl_xor_sync(0xffffffffu, y.x, o), __shfl_xor_sync(0xffffffffu, y.y, o)));
+            z = add2(z, pk(__shfl_xor_sync(0xffffffffu, z.x, o), __shfl_xor_sync(0xffffffffu, z.y, o)));
+        }
+    }
+
+    // F(x_a), F(x_b) of particle i (complete in every thread of the group).
+    __device__ void force(const Smem<NMAX>& P, const K2& k, bool scan_all, float2& fx, float2& fy,
+                          float2& fz) const
+    {
+        fx = fy = fz = pk(0.0f);
+        if (active) {
+            const float4 pxy = P.xy(8 * i);
+            const float2 xi = pk(pxy.x, pxy.y), yi = pk(pxy.z, pxy.w), zi = P.z(8 * i);
+            for_each_candidate(scan_all, [&](int o8) {
+                float2 dx, dy, dz, w, ir2, ir6;
+                const float2 r2 = pair_geom(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
+                const float2 fs = pair_fs(r2, k, w, ir2, ir6);
+                fx = fma2(fs, dx, fx);
+                fy = fma2(fs, dy, fy);
+                fz = fma2(fs, dz, fz);
+            });
+        }
+        group_sum(fx, fy, fz);
+    }
+
+    // (H(x_a) v_a, H(x_b) v_b) of particle i; v is the residual array, vi its own value.
+    __device__ void hvp(const Smem<NMAX>& P, float2 vix, float2 viy, float2 viz, const K2& k,
+                        bool scan_all, float2& hx, float2& hy, float2& hz) const
+    {
+        hx = hy = hz = pk(0.0f);
+        if (active) {
+            const float4 pxy = P.xy(8 * i);
+            const float2 xi = pk(pxy.x, pxy.y), yi = pk(pxy.z, pxy.w), zi = P.z(8 * i);
+            for_each_candidate(scan_all, [&](int o8) {
+                float2 dx, dy, dz, w, ir2, ir6;
+                const float2 r2 = pair_geom(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
+                const float2 fs = pair_fs(r2, k, w, ir2, ir6);                       // -U'/r
+                const float2 Bc = mul2(fma2(w, fma2(k.c3, ir6, k.m7), fs), ir2);     // (U''-U'/r)/r^2
+                const float2 nfs = mul2(fs, k.m1);
+                const float4 vj = P.rxy(o8);
+                const float2 vx = sub2(vix, pk(vj.x, vj.y));
+                const float2 vy = sub2(viy, pk(vj.z, vj.w));
+                const float2 vz = sub2(viz, P.rz(o8));
+                const float2 bd = mul2(Bc, fma2(dz, vz, fma2(dy, vy, mul2(dx, vx))));
+                hx = fma2(nfs, vx, fma2(bd, dx, hx));
+                hy = fma2(nfs, vy, fma2(bd, dy, hy));
+                hz = fma2(nfs, vz, fma2(bd, dz, hz));
+            });
+        }
+        group_sum(hx, hy, hz);
+    }
+};
+
+__device__ __forceinline__ float sq3(float x, float y, float z)
+{
+    return __fmaf_rn(z, z, __fmaf_rn(y, y, x * x));
+}
+
+// One work item: steps [t0, t1) of one chain.
+template <bool GRAD, int NMAX>
+__device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<float>& S,
+                                            unsigned char* smem, const float* __restrict__ pos,
+                                            float* __restrict__ grad, double* __restrict__ partials,
+                                            double* red)
+{
+    const int N = S.N;
+    const Smem<NMAX> P{smem};
+    PairList<NMAX> L;
+    L.init(N, S.tpp, S.lg_tpp, S.cap, P.list());
+    const K2 k(S.k);
+    const float2 na = pk(-k.a), ginv = pk(k.ginv);
+
+    const int t0 = I.t0, t1 = I.t1, T = S.T;
+    const int s = 3 * N;
+    const float* __restrict__ X = pos + S.off + (long long)I.chain * S.chain_len;
+    float* __restrict__ G = GRAD ? grad + S.off + (long long)I.chain * S.chain_len : nullptr;
+    const int i = L.i;
+    const bool lead = L.active && L.q == 0;
+    const int ts = t0 > 0 ? t0 - 1 : t0;  // first slice of the first pair
+
+    // Slices (a, a+1) of particle n into registers (a + 1 <= T for every pair).
+    auto fetch = [&](int a, int n, float (&v)[6]) {
+        const float* A = X + (long long)a * s + n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[2 * c] = __ldg(A + c * N);
+            v[2 * c + 1] = __ldg(A + s + c * N);
+        }
+    };
+    auto store = [&](int n, const float (&v)[6]) {
+        P.xy(8 * n) = make_float4(v[0], v[1], v[2], v[3]);
+        P.z(8 * n) = make_float2(v[4], v[5]);
+    };
+
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        float v[6];
+        fetch(ts, n, v);
+        store(n, v);
+    }
+    __syncthreads();
+
+    float rpx = 0.0f, rpy = 0.0f, rpz = 0.0f;  // r_{a-1}
+    double acc = 0.0;
+    bool built = false;
+
+    for (int a = ts; a < t1; a += 2) {
+        const int b = a + 1;
+        const bool hasb = b < t1;
+        const bool real_a = a >= t0;
+        // Prefetch the next pair's slices, and this particle's x_{b+1}.
+        const bool pf = a + 2 < t1 && (int)threadIdx.x < N;
+        float nv[6];
+        if (pf) fetch(a + 2, threadIdx.x, nv);
+        float xn = 0.0f, yn = 0.0f, zn = 0.0f;
+        if (hasb && L.active) {
+            const float* Xb1 = X + (long long)(b + 1) * s + i;
+            xn = __ldg(Xb1);
+            yn = __ldg(Xb1 + N);
+            zn = __ldg(Xb1 + 2 * N);
+        }
+
+        // Neighbour list valid for both slices?
+        bool ma, mb;
+        L.moved(P, k, ma, mb);
+        bool scan_all = false;
+        if (__syncthreads_or(!built || ma || mb)) {
+            L.build(P, k);
+            built = true;
+            L.moved(P, k, ma, mb);
+            scan_all = __syncthreads_or(mb);
+        }
+
+        float2 fx, fy, fz;
+        L.force(P, k, scan_all, fx, fy, fz);
+        float2 rx = pk(0.0f), ry = pk(0.0f), rz = pk(0.0f);
+        if (L.active) {
+            const float4 pxy = P.xy(8 * i);
+            const float2 pz = P.z(8 * i);
+            // (x_b - x_a, x_{b+1} - x_b) - a (F_a, F_b); the second half only when b is a step.
+            rx = fma2(na, fx, sub2(pk(pxy.y, xn), pk(pxy.x, pxy.y)));
+            ry = fma2(na, fy, sub2(pk(pxy.w, yn), pk(pxy.z, pxy.w)));
+            rz = fma2(na, fz, sub2(pk(pz.y, zn), pz));
+            if (!hasb) rx.y = ry.y = rz.y = 0.0f;
+            if (lead) {
+                if (GRAD) {
+                    P.rxy(8 * i) = make_float4(rx.x, rx.y, ry.x, ry.y);
+                    P.rz(8 * i) = rz;
+                }
+                if (real_a) acc += (double)sq3(rx.x, ry.x, rz.x);
+                if (hasb) acc += (double)sq3(rx.y, ry.y, rz.y);
+            }
+        }
+        if (GRAD) {
+            __syncthreads();
+            float2 hx, hy, hz;
+            L.hvp(P, rx, ry, rz, k, scan_all, hx, hy, hz);
+            if (lead) {
+                // g = (r_prev - r + a H r) / (2 D dt), packed over (a, b).
+                const float2 gx = mul2(fma2(pk(k.a), hx, sub2(pk(rpx, rx.x), rx)), ginv);
+                const float2 gy = mul2(fma2(pk(k.a), hy, sub2(pk(rpy, ry.x), ry)), ginv);
+                const float2 gz = mul2(fma2(pk(k.a), hz, sub2(pk(rpz, rz.x), rz)), ginv);
+                if (real_a) {
+                    float* Ga = G + (long long)a * s + i;
+                    Ga[0] = gx.x;
+                    Ga[N] = gy.x;
+                    Ga[2 * N] = gz.x;
+                }
+                if (hasb) {
+                    float* Gb = G + (long long)b * s + i;
+                    Gb[0] = gx.y;
+                    Gb[N] = gy.y;
+                    Gb[2 * N] = gz.y;
+                }
+            }
+        }
+        rpx = hasb ? rx.y : rx.x;
+        rpy = hasb ? ry.y : ry.x;
+        rpz = hasb ? rz.y : rz.x;
+        __syncthreads();
+        if (pf) store(threadIdx.x, nv);
+        __syncthreads();
+    }
+    if (GRAD && t1 == T && lead) {
+        float* Gt = G + (long long)T * s + i;
+        Gt[0] = rpx * k.ginv;
+        Gt[N] = rpy * k.ginv;
+        Gt[2 * N] = rpz * k.ginv;
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[I.slot] = tot;
+}
+
+// Persistent grid: each CTA takes items from *counter until none is left.
+// Systems must have N <= MAXT (the block size is at most MAXT).
+template <bool GRAD, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+    lj_paired_kernel(const LJItem* __restrict__ items, int n_items,
+                     const LJSysDev<float>* __restrict__ systems, const float* __restrict__ pos,
+                     float* __restrict__ grad, double* __restrict__ partials,
+                     int* __restrict__ counter)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const LJItem I = items[it];
+        const LJSysDev<float> S = systems[I.sys];
+        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red);
+    }
+}
+
+template <bool GRAD>
+auto paired_kernel_ptr(int NT)
+{
+    return NT <= 512 ? lj_paired_kernel<GRAD, 512> : lj_paired_kernel<GRAD, 1024>;
+}
+
+}  // namespace
+
+size_t lj_paired_smem_bytes(int NT, int cap_lane)
+{
+    const size_t nmax = NT <= 512 ? 512 : 1024;
+    return 48 * nmax + (size_t)(cap_lane / 2) * NT * sizeof(uint32_t);
+}
+
+int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad)
+{
+    auto kern = with_grad ? paired_kernel_ptr<true>(NT) : paired_kernel_ptr<false>(NT);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
+                             const float* pos, float* grad, double* partials, int* counter, int NT,
+                             size_t smem, int grid, bool with_grad, cudaStream_t st)
+{
+    if (n_items <= 0) return cudaSuccess;
+    if (NT > 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    auto kern = with_grad ? paired_kernel_ptr<true>(NT) : paired_kernel_ptr<false>(NT);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, smem, st>>>(items, n_items, static_cast<const LJSysDev<float>*>(sys_table),
+                                 pos, grad, partials, counter);
+    return cudaGetLastError();
+}
+
+}  // namespace pamd

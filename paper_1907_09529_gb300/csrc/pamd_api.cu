@@ -86,6 +86,7 @@ struct Plan {
     double* d_part_qr = nullptr;
     // LJ work items (persistent kernel)
     int lj_NT = 0, lj_nmax = 0, lj_grid_grad = 0, lj_grid_nograd = 0;
+    bool lj_paired = false;  // single precision: two steps per thread (lj_paired.cu)
     size_t lj_smem = 0;
     std::vector<unsigned char> h_lj_sys;  // host copy of the system table
     size_t lj_sys_stride = 0;
@@ -372,11 +373,17 @@ int build_plan(const pamd_problem* p, Plan** out)
         if (nlj) {
             const int NT = choose_lj_block(p);
             const size_t v4 = P->fp64 ? 32 : 16;
-            const int budget = (NT <= 512 && !P->fp64 && g_tune_override.maxnb <= 0)
+            // Single precision runs the paired-step kernel, one CTA per SM: its list
+            // may use all the shared memory beside two packed slices of 32 bytes.
+            P->lj_paired = !P->fp64 && std::getenv("PAMD_LJ_ONE_STEP") == nullptr;
+            const long long slices = P->lj_paired ? 48LL * (NT <= 512 ? 512 : 1024) : 3 * (long long)nmax * v4;
+            const int budget = (NT <= 512 && !P->fp64 && !P->lj_paired && g_tune_override.maxnb <= 0)
                                    ? 113 * 1024
                                    : max_dynamic_smem() - 1024;
-            const int cap_lane_max =
-                std::max(1, (int)((budget - 3 * (long long)nmax * v4) / (2 * (long long)NT)));
+            // (the one-step Euler kernel shares the capacity: its slices must fit too)
+            const long long slices_euler = 3 * (long long)nmax * v4;
+            const int cap_lane_max = std::max(
+                1, (int)((budget - std::max(slices, slices_euler)) / (2 * (long long)NT)));
             int cap_used = 1;
             std::vector<double> cost;
             for (int q = 0; q < (int)P->sys.size(); ++q) {
@@ -415,14 +422,17 @@ int build_plan(const pamd_problem* p, Plan** out)
             }
             P->lj_NT = NT;
             P->lj_nmax = nmax;
-            P->lj_smem = lj_smem_bytes(nmax, NT, cap_used, P->fp64);
+            P->lj_smem = P->lj_paired ? lj_paired_smem_bytes(NT, cap_used)
+                                      : lj_smem_bytes(nmax, NT, cap_used, P->fp64);
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int bg = P->fp64 ? lj_blocks_per_sm<double>(NT, P->lj_smem, true)
-                                   : lj_blocks_per_sm<float>(NT, P->lj_smem, true);
-            const int bn = P->fp64 ? lj_blocks_per_sm<double>(NT, P->lj_smem, false)
-                                   : lj_blocks_per_sm<float>(NT, P->lj_smem, false);
+            const int bg = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, true)
+                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, true)
+                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, true);
+            const int bn = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, false)
+                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, false)
+                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, false);
             if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
             P->lj_grid_grad = std::max(1, std::min((int)items.size(), bg * sms));
             P->lj_grid_nograd = std::max(1, std::min((int)items.size(), bn * sms));
@@ -431,8 +441,8 @@ int build_plan(const pamd_problem* p, Plan** out)
             else
                 fill_lj_sys<float>(P.get(), p);
             if (std::getenv("PAMD_DEBUG_PLAN")) {
-                std::fprintf(stderr, "pamd plan: NT=%d nmax=%d smem=%zu blocks/SM grad=%d nograd=%d "
-                             "grid=%d items=%zu\n", NT, nmax, P->lj_smem, bg, bn, P->lj_grid_grad,
+                std::fprintf(stderr, "pamd plan: paired=%d NT=%d nmax=%d smem=%zu blocks/SM grad=%d nograd=%d "
+                             "grid=%d items=%zu\n", (int)P->lj_paired, NT, nmax, P->lj_smem, bg, bn, P->lj_grid_grad,
                              items.size());
                 for (auto& si : P->sys)
                     if (si.kind == PAMD_LJ)
@@ -531,18 +541,22 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
     }
     if (P->n_lj_items > 0) {
         const int grid = with_grad ? P->lj_grid_grad : P->lj_grid_nograd;
+        auto launch = [&](const LJItem* items, int n, int g) {
+            if (std::is_same<R, float>::value && P->lj_paired)
+                return launch_lj_paired(items, n, P->d_lj_sys, (const float*)pos,
+                                        (float*)grad, P->d_part_S, P->d_counter, P->lj_NT, P->lj_smem,
+                                        g, with_grad, st);
+            return launch_lj_items<R>(items, n, P->d_lj_sys, P->lj_nmax, pos, grad, P->d_part_S,
+                                      P->d_counter, P->lj_NT, P->lj_smem, g, with_grad, st);
+        };
         if (!one) {
-            PAMD_CUDA_TRY(launch_lj_items<R>(P->d_lj_items, P->n_lj_items, P->d_lj_sys, P->lj_nmax, pos,
-                                             grad, P->d_part_S, P->d_counter, P->lj_NT, P->lj_smem,
-                                             grid, with_grad, st));
+            PAMD_CUDA_TRY(launch(P->d_lj_items, P->n_lj_items, grid));
         } else {
             for (int c = 0; c < P->n_chains; ++c) {
                 const int f = P->lj_chain_first[c];
                 if (f < 0) continue;
                 const int n = P->lj_chain_count[c];
-                PAMD_CUDA_TRY(launch_lj_items<R>(P->d_lj_items + f, n, P->d_lj_sys, P->lj_nmax, pos,
-                                                 grad, P->d_part_S, P->d_counter, P->lj_NT, P->lj_smem,
-                                                 std::min(grid, n), with_grad, st));
+                PAMD_CUDA_TRY(launch(P->d_lj_items + f, n, std::min(grid, n)));
             }
         }
     }

@@ -256,6 +256,16 @@ cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_ta
                             const R* pos, R* grad, double* partials, int* counter, int NT,
                             size_t smem, int grid, bool with_grad, cudaStream_t st);
 
+// Single-precision action (+ adjoint) with two consecutive steps per thread and
+// packed f32x2 pair arithmetic (lj_paired.cu), for systems of N <= NT <= 1024.
+// Shared memory: positions and residuals of two slices (48 bytes per particle
+// slot, 512 or 1024 slots) and cap_lane list entries per thread, two to a word.
+size_t lj_paired_smem_bytes(int NT, int cap_lane);
+int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad);
+cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
+                             const float* pos, float* grad, double* partials, int* counter, int NT,
+                             size_t smem, int grid, bool with_grad, cudaStream_t st);
+
 cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, int T, int n_chains,
                                   long long sys_offset, double L, double rc, cudaStream_t st);
 
