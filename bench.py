@@ -139,6 +139,7 @@ class ClockSampler:
 #: Sources that define each profiled kernel (with the shared header).
 KERNEL_SOURCES = {
     "lj_action_kernel": ("lj_kernels.cu", "pamd_internal.cuh"),
+    "lj_paired_kernel": ("lj_paired.cu", "pamd_internal.cuh"),
     "ho_vec_kernel": ("ho_kernels.cu", "pamd_internal.cuh"),
     "fragment_line_kernel": ("fragment_kernels.cu", "fragment.cuh", "pamd_internal.cuh"),
 }
@@ -508,8 +509,8 @@ def main():
         achieved = flops / (ms_kernel * 1e-3) / 1e12
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(args.config, "lj_action_kernel"),
-                "kernel": "lj_action_kernel<float,TPP,true>",
+                "frac": achieved / peak, "traffic": profiled_traffic(args.config, "lj_paired_kernel"),
+                "kernel": "lj_paired_kernel<GRAD=1,512>",
                 "peak_note": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
                 "pairs_per_launch": pairs, "flops_per_launch": flops, "kernel_ms": ms_kernel}
     else:

@@ -28,10 +28,17 @@
 // (a, a+1).  An item that does not start at step 0 begins with the pair
 // (t0-1, t0), whose first half only supplies the residual r_{t0-1}.
 //
-// Neighbour lists.  A Verlet list of radius rc + skin, built at the first slice
-// of a pair, is used while every particle stays within skin/2 of where it was at
-// the build; if one step breaks that (a path far from Brownian), the pair scans
-// all candidates.  Candidates are visited in increasing j in every case, so each
+// Neighbour lists.  A Verlet list of radius rc + skin, built from the positions
+// at a reference slice, is exact at every slice where no particle is more than
+// skin/2 away from its reference position.  Along a Brownian path the distance
+// from a slice grows like sqrt(|t - t_ref|) on both sides, so a list is built
+// about a reference slice ahead of the current one -- 3/8 of the previous list's
+// lifetime ahead (measured on LJ N=500: 1/2 sits too close to the point where the
+// current pair already fails the test, 1/4 gains less) -- and lasts longer than a
+// list built at the current slice.  If the current pair is not within
+// skin/2 of that reference, the list is rebuilt at the pair's first slice; if one
+// step breaks even that (a path far from Brownian), the pair scans all
+// candidates.  Candidates are visited in increasing j in every case, so each
 // force and Hessian sum runs over the in-cutoff pairs in one fixed order whatever
 // the tiling, skin or list capacity, and the results are bitwise independent of
 // them.
@@ -163,25 +170,41 @@ struct PairList {
         reinterpret_cast<uint16_t*>(nbr + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
     }
 
-    // Verlet list at slice a: candidates j = q (mod tpp), two per packed operation.
+    // Reference position of particle j: slice a of the current pair (AHEAD
+    // false), or the reference slice staged as {x, y, z, 0} in the residual
+    // array (AHEAD true).
+    template <bool AHEAD>
+    __device__ __forceinline__ float3 ref_pos(const Smem<NMAX>& P, int j) const
+    {
+        if (AHEAD) {
+            const float4 v = P.rxy(8 * j);
+            return make_float3(v.x, v.y, v.z);
+        }
+        const float4 v = P.xy(8 * j);
+        return make_float3(v.x, v.z, P.z(8 * j).x);
+    }
+
+    // Verlet list at the reference positions: candidates j = q (mod tpp), two
+    // per packed operation.
+    template <bool AHEAD>
     __device__ void build(const Smem<NMAX>& P, const K2& k)
     {
         cnt = 0;
         ovf = false;
         if (!active) return;
-        const int oi = 8 * i;
-        xr = P.xy(oi).x;
-        yr = P.xy(oi).z;
-        zr = P.z(oi).x;
+        const float3 pi = ref_pos<AHEAD>(P, i);
+        xr = pi.x;
+        yr = pi.y;
+        zr = pi.z;
         const float2 xi = pk(xr), yi = pk(yr), zi = pk(zr);
         int c = 0;
         for (int j = q; j < N; j += 2 * tpp) {
             const int j2 = j + tpp;
             const int j2c = j2 < N ? j2 : j;
-            const float4 A = P.xy(8 * j), B = P.xy(8 * j2c);
+            const float3 A = ref_pos<AHEAD>(P, j), B = ref_pos<AHEAD>(P, j2c);
             float2 dx = sub2(xi, pk(A.x, B.x));
-            float2 dy = sub2(yi, pk(A.z, B.z));
-            float2 dz = sub2(zi, pk(P.z(8 * j).x, P.z(8 * j2c).x));
+            float2 dy = sub2(yi, pk(A.y, B.y));
+            float2 dz = sub2(zi, pk(A.z, B.z));
             dx = fma2(k.nL, add2(fma2(dx, k.iL, k.mag), k.nmag), dx);
             dy = fma2(k.nL, add2(fma2(dy, k.iL, k.mag), k.nmag), dy);
             dz = fma2(k.nL, add2(fma2(dz, k.iL, k.mag), k.nmag), dz);
@@ -296,11 +319,13 @@ __device__ __forceinline__ float sq3(float x, float y, float z)
 }
 
 // One work item: steps [t0, t1) of one chain.
+// ahead: how many steps past the current pair the next list's reference slice
+// lies (carried from item to item; adapted to the observed list lifetime).
 template <bool GRAD, int NMAX>
 __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<float>& S,
                                             unsigned char* smem, const float* __restrict__ pos,
                                             float* __restrict__ grad, double* __restrict__ partials,
-                                            double* red)
+                                            double* red, int& ahead)
 {
     const int N = S.N;
     const Smem<NMAX> P{smem};
@@ -341,6 +366,7 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
     float rpx = 0.0f, rpy = 0.0f, rpz = 0.0f;  // r_{a-1}
     double acc = 0.0;
     bool built = false;
+    int a_built = ts;  // first slice of the pair at which the current list was built
 
     for (int a = ts; a < t1; a += 2) {
         const int b = a + 1;
@@ -363,10 +389,29 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
         L.moved(P, k, ma, mb);
         bool scan_all = false;
         if (__syncthreads_or(!built || ma || mb)) {
-            L.build(P, k);
+            if (built) ahead = max(1, min(64, (3 * (a - a_built)) / 8));
+            const int c = min(a + ahead, t1);  // reference slice (c <= T)
+            bool ok = false;
+            if (c > b) {
+                // Stage slice c as {x, y, z, 0} in the residual array (free until
+                // the residuals of this pair are written, after the next barrier).
+                for (int n = threadIdx.x; n < N; n += blockDim.x) {
+                    const float* A = X + (long long)c * s + n;
+                    P.rxy(8 * n) = make_float4(__ldg(A), __ldg(A + N), __ldg(A + 2 * N), 0.0f);
+                }
+                __syncthreads();
+                L.template build<true>(P, k);
+                L.moved(P, k, ma, mb);
+                ok = !__syncthreads_or(ma || mb);
+            }
+            if (!ok) {
+                L.template build<false>(P, k);
+                L.moved(P, k, ma, mb);
+                scan_all = __syncthreads_or(mb);
+                ahead = 1;
+            }
             built = true;
-            L.moved(P, k, ma, mb);
-            scan_all = __syncthreads_or(mb);
+            a_built = a;
         }
 
         float2 fx, fy, fz;
@@ -441,6 +486,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ int s_item;
+    int ahead = 4;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -449,7 +495,7 @@ __global__ void __launch_bounds__(MAXT, 1)
         if (it >= n_items) break;
         const LJItem I = items[it];
         const LJSysDev<float> S = systems[I.sys];
-        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red);
+        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red, ahead);
     }
 }
 
