@@ -118,9 +118,10 @@ def test_edge_cases_tiny_paths(pamd):
 
 @pytest.mark.parametrize("name", ["lj108", "lj500"])
 def test_results_independent_of_tiling(pamd, name):
-    """Candidate order is fixed, so the gradient is bitwise the same for any tile,
-    skin, list capacity (including the overflow path) and thread split.  lj500's
-    box is large enough for the no-shift list segment; lj108's is not."""
+    """Candidate order is fixed, so S and the gradient are bitwise the same for any
+    tile, skin (including skins small enough that single steps fall back to the
+    all-candidate scan) and list capacity (including the overflow path).  In
+    lj108's box rc + skin exceeds L/2; in lj500's it does not."""
     w = inputs.workload(name, "small")
     paths = start_paths(w, "fp32")
     outs = []
