@@ -94,6 +94,10 @@ struct Plan {
     LJItem* d_lj_items = nullptr;
     int n_lj_items = 0;
     std::vector<int> lj_chain_first, lj_chain_count;  // per global chain (plain form)
+    // the same items grouped by chain: chain c owns [lj_grp_first[c], lj_grp_first[c + 1])
+    std::vector<int> lj_grp_first;
+    LJItem* d_lj_items_grp = nullptr;
+    std::vector<ChainSlots> h_E_slots;  // per chain: its element blocks in h_all
     int* d_counter = nullptr;
     int* d_err = nullptr;  // device status word (PAMD_OK or PAMD_ERR_NONFINITE)
     // update workspace (allocated on first use)
@@ -114,10 +118,19 @@ struct Plan {
     int* d_stage_int = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::vector<void*> allocs;
+    // host-buffer pipeline: copy streams, a second compute stream, events and one LJ
+    // work counter per chunk (created on first use)
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_cmp = nullptr;
+    std::vector<cudaEvent_t> events;
+    int* d_chunk_counters = nullptr;
 
     ~Plan()
     {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        if (s_in) cudaStreamDestroy(s_in);
+        if (s_out) cudaStreamDestroy(s_out);
+        if (s_cmp) cudaStreamDestroy(s_cmp);
         for (void* p : allocs) cudaFree(p);
     }
     template <typename T>
@@ -359,7 +372,8 @@ int build_plan(const pamd_problem* p, Plan** out)
     }
     int slot = (int)P->h_ho.size();
     // LJ: common block size, shared-memory budget, per-system shapes, items.
-    std::vector<LJItem> items;
+    std::vector<LJItem> items, grouped;
+    std::vector<int> item_chain;  // global chain of each item
     P->lj_chain_first.assign(chain, -1);
     P->lj_chain_count.assign(chain, 0);
     {
@@ -407,10 +421,22 @@ int build_plan(const pamd_problem* p, Plan** out)
                         it.t1 = std::min(si.T, it.t0 + si.tune.tile_steps);
                         it.slot = slot + b * si.n_tiles + tl;
                         items.push_back(it);
+                        item_chain.push_back(c);
                         cost.push_back((double)si.N * si.tune.maxnb * si.tune.tpp * (it.t1 - it.t0 + 1));
                     }
                 }
                 slot += si.chains * si.n_tiles;
+            }
+            // Chain-grouped copy (chains in order, each chain's items largest first) for
+            // launches over a range of chains.
+            {
+                std::vector<int> ord(items.size());
+                for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+                std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+                    const int ca = item_chain[a], cb = item_chain[b];
+                    return ca != cb ? ca < cb : cost[a] > cost[b];
+                });
+                for (int q : ord) grouped.push_back(items[q]);
             }
             if (!one) {  // largest items first
                 std::vector<int> ord(items.size());
@@ -454,6 +480,9 @@ int build_plan(const pamd_problem* p, Plan** out)
     }
     P->n_lj_items = (int)items.size();
     P->n_S_slots = slot;
+    P->lj_grp_first.assign(chain + 1, 0);
+    for (int c = 0; c < chain; ++c) P->lj_grp_first[c + 1] = P->lj_grp_first[c] + P->lj_chain_count[c];
+    P->h_E_slots = Eslots;
     int rc;
     if ((rc = P->alloc(&P->d_all, sizeof(ElemBlock) * P->h_all.size()))) return rc;
     if ((rc = P->alloc(&P->d_ho, sizeof(ElemBlock) * P->h_ho.size()))) return rc;
@@ -463,12 +492,16 @@ int build_plan(const pamd_problem* p, Plan** out)
     if ((rc = P->alloc(&P->d_part_qf, sizeof(double) * P->h_all.size()))) return rc;
     if ((rc = P->alloc(&P->d_part_qr, sizeof(double) * P->h_all.size()))) return rc;
     if ((rc = P->alloc(&P->d_lj_items, sizeof(LJItem) * items.size()))) return rc;
+    if ((rc = P->alloc(&P->d_lj_items_grp, sizeof(LJItem) * grouped.size()))) return rc;
     if ((rc = P->alloc(&P->d_lj_sys, P->h_lj_sys.size()))) return rc;
     if ((rc = P->alloc(&P->d_counter, sizeof(int)))) return rc;
     if ((rc = P->alloc(&P->d_err, sizeof(int)))) return rc;
     PAMD_CUDA_TRY(cudaMemset(P->d_err, 0, sizeof(int)));
     if (!items.empty())
         PAMD_CUDA_TRY(cudaMemcpy(P->d_lj_items, items.data(), sizeof(LJItem) * items.size(),
+                                 cudaMemcpyHostToDevice));
+    if (!grouped.empty())
+        PAMD_CUDA_TRY(cudaMemcpy(P->d_lj_items_grp, grouped.data(), sizeof(LJItem) * grouped.size(),
                                  cudaMemcpyHostToDevice));
     if (!P->h_lj_sys.empty())
         PAMD_CUDA_TRY(cudaMemcpy(P->d_lj_sys, P->h_lj_sys.data(), P->h_lj_sys.size(),
@@ -515,21 +548,26 @@ bool is_host_ptr(const void* ptr)
     return !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
 }
 
-// S (and grad) of every chain into S_out, from device pointers.
+// S (and grad) of chains [c0, c1) into S_out (indexed by global chain), from
+// device pointers; c1 < 0 means every chain.  The results of a chain do not
+// depend on the range it is computed in.
 template <typename R>
 int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_out, bool with_grad,
-               cudaStream_t st)
+               cudaStream_t st, int c0 = 0, int c1 = -1, int* counter = nullptr)
 {
+    if (c1 < 0) c1 = P->n_chains;
+    if (!counter) counter = P->d_counter;  // LJ work-queue counter of this launch sequence
+    const bool all = c0 == 0 && c1 == P->n_chains;
     const double a = p->beta * p->D * p->dt, ginv = 1.0 / (2.0 * p->D * p->dt);
     const bool one = (p->flags & PAMD_FLAG_ONE_CHAIN_PER_LAUNCH) != 0;
     // harmonic systems: one launch per system (per chain in the plain form)
     for (const auto& si : P->sys) {
         if (si.kind != PAMD_HARMONIC) continue;
+        const int lo_c = std::max(c0, si.chain0), hi_c = std::min(c1, si.chain0 + si.chains);
+        if (lo_c >= hi_c) continue;
         const int sz = si.d * si.N;
         const long long lo = si.off, hi = si.off + si.chain_len * si.chains;
-        for (int c = one ? 0 : -1; c < (one ? si.chains : 0); ++c) {
-            const int b0 = one ? P->ho_chain_first[si.chain0 + c] : si.ho_b0;
-            const int nb = one ? P->ho_chain_count[si.chain0 + c] : si.ho_b1 - si.ho_b0;
+        auto ho = [&](int b0, int nb) -> int {
             if (std::is_same<R, float>::value && sz <= 4)
                 PAMD_CUDA_TRY(launch_ho_action_vec(P->d_ho + b0, nb, sz, (const float*)pos,
                                                    (float*)grad, P->d_part_S, b0, a, ginv, with_grad,
@@ -537,6 +575,16 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
             else
                 PAMD_CUDA_TRY(launch_ho_action<R>(P->d_ho + b0, nb, P->max_s_ho, pos, grad, P->d_part_S,
                                                   b0, a, ginv, with_grad, st));
+            return PAMD_OK;
+        };
+        int rc;
+        if (one) {
+            for (int c = lo_c; c < hi_c; ++c)
+                if ((rc = ho(P->ho_chain_first[c], P->ho_chain_count[c]))) return rc;
+        } else {
+            const int b0 = P->ho_chain_first[lo_c];
+            const int b1 = P->ho_chain_first[hi_c - 1] + P->ho_chain_count[hi_c - 1];
+            if ((rc = ho(b0, b1 - b0))) return rc;
         }
     }
     if (P->n_lj_items > 0) {
@@ -544,45 +592,157 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
         auto launch = [&](const LJItem* items, int n, int g) {
             if (std::is_same<R, float>::value && P->lj_paired)
                 return launch_lj_paired(items, n, P->d_lj_sys, (const float*)pos,
-                                        (float*)grad, P->d_part_S, P->d_counter, P->lj_NT, P->lj_smem,
+                                        (float*)grad, P->d_part_S, counter, P->lj_NT, P->lj_smem,
                                         g, with_grad, st);
             return launch_lj_items<R>(items, n, P->d_lj_sys, P->lj_nmax, pos, grad, P->d_part_S,
-                                      P->d_counter, P->lj_NT, P->lj_smem, g, with_grad, st);
+                                      counter, P->lj_NT, P->lj_smem, g, with_grad, st);
         };
-        if (!one) {
-            PAMD_CUDA_TRY(launch(P->d_lj_items, P->n_lj_items, grid));
-        } else {
-            for (int c = 0; c < P->n_chains; ++c) {
+        if (one) {
+            for (int c = c0; c < c1; ++c) {
                 const int f = P->lj_chain_first[c];
                 if (f < 0) continue;
                 const int n = P->lj_chain_count[c];
                 PAMD_CUDA_TRY(launch(P->d_lj_items + f, n, std::min(grid, n)));
             }
+        } else if (all) {
+            PAMD_CUDA_TRY(launch(P->d_lj_items, P->n_lj_items, grid));
+        } else {
+            const int f = P->lj_grp_first[c0], n = P->lj_grp_first[c1] - f;
+            if (n > 0) PAMD_CUDA_TRY(launch(P->d_lj_items_grp + f, n, std::min(grid, n)));
         }
     }
-    PAMD_CUDA_TRY(launch_finalize(P->d_part_S, P->d_S_slots, P->n_chains, 1.0 / (4.0 * p->D * p->dt),
-                                  S_out, st, P->d_err));
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_S, P->d_S_slots + c0, c1 - c0, 1.0 / (4.0 * p->D * p->dt),
+                                  S_out + c0, st, P->d_err));
     return PAMD_OK;
 }
 
+// One path update of chains [c0, c1) (c1 < 0: every chain); arrays indexed by
+// global chain.
 template <typename R>
 int run_one_update(const pamd_problem* p, Plan* P, R* pos, R* grad, double* S, const R* noise,
-                   const double* log_u, int* n_acc, double* la, int u, cudaStream_t st)
+                   const double* log_u, int* n_acc, double* la, int u, cudaStream_t st, int c0 = 0,
+                   int c1 = -1, int* counter = nullptr)
 {
-    const int nb = (int)P->h_all.size();
+    if (c1 < 0) c1 = P->n_chains;
+    const int eb0 = P->h_E_slots[c0].begin, eb1 = P->h_E_slots[c1 - 1].end;
     R* prop = reinterpret_cast<R*>(P->d_prop);
     R* gprop = reinterpret_cast<R*>(P->d_gprop);
-    PAMD_CUDA_TRY(launch_mala_propose<R>(P->d_all, nb, pos, grad, noise, prop, P->d_part_qf, P->d_md,
-                                         u, st));
-    int rc = run_action<R>(p, P, prop, gprop, P->d_Sprop, true, st);
+    PAMD_CUDA_TRY(launch_mala_propose<R>(P->d_all + eb0, eb1 - eb0, pos, grad, noise, prop,
+                                         P->d_part_qf + eb0, P->d_md, u, st));
+    int rc = run_action<R>(p, P, prop, gprop, P->d_Sprop, true, st, c0, c1, counter);
     if (rc) return rc;
-    PAMD_CUDA_TRY(launch_mala_reverse<R>(P->d_all, nb, pos, prop, gprop, P->d_part_qr, P->d_md, st));
-    PAMD_CUDA_TRY(launch_finalize(P->d_part_qf, P->d_E_slots, P->n_chains, 1.0, P->d_qf, st));
-    PAMD_CUDA_TRY(launch_finalize(P->d_part_qr, P->d_E_slots, P->n_chains, 1.0, P->d_qr, st));
-    PAMD_CUDA_TRY(launch_mala_accept(P->n_chains, S, P->d_Sprop, P->d_qf, P->d_qr, log_u, P->d_md, u,
+    PAMD_CUDA_TRY(launch_mala_reverse<R>(P->d_all + eb0, eb1 - eb0, pos, prop, gprop,
+                                         P->d_part_qr + eb0, P->d_md, st));
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_qf, P->d_E_slots + c0, c1 - c0, 1.0, P->d_qf + c0, st));
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_qr, P->d_E_slots + c0, c1 - c0, 1.0, P->d_qr + c0, st));
+    PAMD_CUDA_TRY(launch_mala_accept(c0, c1 - c0, S, P->d_Sprop, P->d_qf, P->d_qr, log_u, P->d_md, u,
                                      P->d_flag, n_acc, la, st));
-    PAMD_CUDA_TRY(launch_mala_commit<R>(P->d_all, nb, pos, grad, prop, gprop, P->d_flag, S, P->d_Sprop,
-                                        st));
+    PAMD_CUDA_TRY(launch_mala_commit<R>(P->d_all + eb0, eb1 - eb0, pos, grad, prop, gprop, P->d_flag,
+                                        S, P->d_Sprop, st));
+    return PAMD_OK;
+}
+
+// Path updates with host buffers (no explicit noise or uniforms), pipelined over
+// chunks of chains: chunk k's inputs are copied in on one stream while earlier
+// chunks are updated and copied back on others.  Updates alternate between the
+// caller's stream and a second compute stream, each chunk with its own LJ work
+// counter, so that the last items of one chunk overlap the next chunk.  Chains
+// are independent, so the results equal those of one update over all.
+template <typename R>
+int path_update_pipelined(const pamd_problem* prob, Plan* P, void* pos, void* grad, double* S,
+                          int n_updates, int* n_accepted, double* log_alpha, cudaStream_t st)
+{
+    int rc;
+    const size_t esz = P->esz;
+    const int nc = P->n_chains;
+    const size_t bytes = esz * (size_t)P->span;
+    const bool hp = is_host_ptr(pos), hg = is_host_ptr(grad), hS = is_host_ptr(S);
+    const bool hn = n_accepted && is_host_ptr(n_accepted);
+    const bool hl = log_alpha && is_host_ptr(log_alpha);
+    if (hp && !P->d_stage_pos && (rc = P->alloc(&P->d_stage_pos, bytes))) return rc;
+    if (hg && !P->d_stage_grad && (rc = P->alloc(&P->d_stage_grad, bytes))) return rc;
+    if (hS && !P->d_stage_S && (rc = P->alloc(&P->d_stage_S, sizeof(double) * nc))) return rc;
+    if (hn && !P->d_stage_int && (rc = P->alloc(&P->d_stage_int, sizeof(int) * nc))) return rc;
+    if (hl && !P->d_stage_dbl && (rc = P->alloc(&P->d_stage_dbl, sizeof(double) * nc))) return rc;
+    char* dpos = hp ? (char*)P->d_stage_pos : (char*)pos;
+    char* dgrad = hg ? (char*)P->d_stage_grad : (char*)grad;
+    double* dS = hS ? P->d_stage_S : S;
+    int* dnacc = hn ? P->d_stage_int : n_accepted;
+    double* dla = hl ? P->d_stage_dbl : log_alpha;
+    constexpr int kMaxChunks = 8;
+    if (!P->s_in) {
+        PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&P->s_in, cudaStreamNonBlocking));
+        PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&P->s_out, cudaStreamNonBlocking));
+        PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&P->s_cmp, cudaStreamNonBlocking));
+    }
+    if (!P->d_chunk_counters && (rc = P->alloc(&P->d_chunk_counters, sizeof(int) * kMaxChunks)))
+        return rc;
+    while ((int)P->events.size() < 2 * kMaxChunks + 2) {
+        cudaEvent_t e;
+        PAMD_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        P->events.push_back(e);
+    }
+    // Element extent of each chain, and chunk boundaries balanced by elements.
+    auto e_begin = [&](int c) { return P->h_all[P->h_E_slots[c].begin].chain_base; };
+    auto e_end = [&](int c) {
+        const ElemBlock& B = P->h_all[P->h_E_slots[c].begin];
+        return B.chain_base + B.chain_len;
+    };
+    const int K = std::min(nc, kMaxChunks);
+    long long total = 0;
+    for (int c = 0; c < nc; ++c) total += e_end(c) - e_begin(c);
+    std::vector<int> cut(K + 1, nc);
+    cut[0] = 0;
+    {
+        long long run = 0;
+        int k = 1;
+        for (int c = 0; c < nc && k < K; ++c) {
+            run += e_end(c) - e_begin(c);
+            // close chunk k-1 after chain c once it holds its share, leaving a chain per later chunk
+            if ((run * K >= total * k || nc - (c + 1) == K - k) && nc - (c + 1) >= K - k) cut[k++] = c + 1;
+        }
+    }
+    cudaEvent_t ev_start = P->events[2 * kMaxChunks], ev_fin = P->events[2 * kMaxChunks + 1];
+    PAMD_CUDA_TRY(cudaEventRecord(ev_start, st));  // host buffers may be written by earlier work on st
+    PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_in, ev_start, 0));
+    PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_cmp, ev_start, 0));
+    for (int k = 0; k < K; ++k) {
+        const int c0 = cut[k], c1 = cut[k + 1];
+        if (c0 >= c1) continue;
+        const long long e0 = e_begin(c0), e1 = e_end(c1 - 1);
+        const size_t off = esz * (size_t)e0, nb = esz * (size_t)(e1 - e0);
+        if (hp) PAMD_CUDA_TRY(cudaMemcpyAsync(dpos + off, (char*)pos + off, nb, cudaMemcpyHostToDevice, P->s_in));
+        if (hg) PAMD_CUDA_TRY(cudaMemcpyAsync(dgrad + off, (char*)grad + off, nb, cudaMemcpyHostToDevice, P->s_in));
+        if (hS)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(dS + c0, S + c0, sizeof(double) * (c1 - c0), cudaMemcpyHostToDevice,
+                                          P->s_in));
+        if (hn)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(dnacc + c0, n_accepted + c0, sizeof(int) * (c1 - c0),
+                                          cudaMemcpyHostToDevice, P->s_in));
+        cudaStream_t cs = (k & 1) ? P->s_cmp : st;
+        PAMD_CUDA_TRY(cudaEventRecord(P->events[2 * k], P->s_in));
+        PAMD_CUDA_TRY(cudaStreamWaitEvent(cs, P->events[2 * k], 0));
+        for (int u = 0; u < n_updates; ++u)
+            if ((rc = run_one_update<R>(prob, P, (R*)dpos, (R*)dgrad, dS, nullptr, nullptr, dnacc, dla,
+                                        u, cs, c0, c1, P->d_chunk_counters + k)))
+                return rc;
+        PAMD_CUDA_TRY(cudaEventRecord(P->events[2 * k + 1], cs));
+        PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_out, P->events[2 * k + 1], 0));
+        if (hp) PAMD_CUDA_TRY(cudaMemcpyAsync((char*)pos + off, dpos + off, nb, cudaMemcpyDeviceToHost, P->s_out));
+        if (hg) PAMD_CUDA_TRY(cudaMemcpyAsync((char*)grad + off, dgrad + off, nb, cudaMemcpyDeviceToHost, P->s_out));
+        if (hS)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(S + c0, dS + c0, sizeof(double) * (c1 - c0), cudaMemcpyDeviceToHost,
+                                          P->s_out));
+        if (hn)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(n_accepted + c0, dnacc + c0, sizeof(int) * (c1 - c0),
+                                          cudaMemcpyDeviceToHost, P->s_out));
+        if (hl)
+            PAMD_CUDA_TRY(cudaMemcpyAsync(log_alpha + c0, dla + c0, sizeof(double) * (c1 - c0),
+                                          cudaMemcpyDeviceToHost, P->s_out));
+    }
+    PAMD_CUDA_TRY(cudaEventRecord(ev_fin, P->s_out));
+    PAMD_CUDA_TRY(cudaStreamWaitEvent(st, ev_fin, 0));
+    PAMD_CUDA_TRY(cudaStreamSynchronize(st));
     return PAMD_OK;
 }
 
@@ -717,6 +877,13 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
     const bool host = is_host_ptr(pos) || is_host_ptr(grad) || is_host_ptr(S) ||
                       is_host_ptr(noise) || is_host_ptr(log_u) || is_host_ptr(n_accepted) ||
                       is_host_ptr(log_alpha);
+    if (host && !noise && !log_u && P->n_chains >= 2) {
+        PAMD_CUDA_TRY(launch_set_mala_params(P->d_md, seed, counter, h, st));
+        return P->fp64 ? path_update_pipelined<double>(prob, P, pos, grad, S, n_updates, n_accepted,
+                                                       log_alpha, st)
+                       : path_update_pipelined<float>(prob, P, pos, grad, S, n_updates, n_accepted,
+                                                      log_alpha, st);
+    }
     void *dpos = pos, *dgrad = grad;
     double* dS = S;
     const void* dnoise = noise;

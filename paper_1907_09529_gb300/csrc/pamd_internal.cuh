@@ -298,7 +298,8 @@ template <typename R>
 cudaError_t launch_mala_reverse(const ElemBlock* blocks, int n_blocks, const R* pos, const R* prop,
                                 const R* grad_prop, double* part_qr, const MalaDev* md,
                                 cudaStream_t st);
-cudaError_t launch_mala_accept(int n_chains, const double* S, const double* S_prop,
+// Accept test for chains [chain0, chain0 + n_chains) (arrays indexed by global chain).
+cudaError_t launch_mala_accept(int chain0, int n_chains, const double* S, const double* S_prop,
                                const double* qf, const double* qr, const double* log_u,
                                const MalaDev* md, int update_index, int* accept_flag,
                                int* n_accepted, double* log_alpha, cudaStream_t st);

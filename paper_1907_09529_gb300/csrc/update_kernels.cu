@@ -122,15 +122,17 @@ __global__ void __launch_bounds__(kElemThreads)
     if (threadIdx.x == 0) part_qr[blockIdx.x] = tot;
 }
 
-__global__ void mala_accept_kernel(int n_chains, const double* __restrict__ S,
+// Chains [chain0, chain0 + n_chains); every array is indexed by the global chain.
+__global__ void mala_accept_kernel(int chain0, int n_chains, const double* __restrict__ S,
                                    const double* __restrict__ S_prop, const double* __restrict__ qf,
                                    const double* __restrict__ qr, const double* __restrict__ log_u,
                                    const MalaDev* __restrict__ md, int update_index,
                                    int* __restrict__ accept_flag, int* __restrict__ n_accepted,
                                    double* __restrict__ log_alpha)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_chains) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_chains) return;
+    const int c = chain0 + q;
     const double h4 = 4.0 * md->h;
     const double la = (S[c] - S_prop[c]) - qr[c] / h4 + qf[c] / h4;
     double lu;
@@ -186,7 +188,7 @@ cudaError_t launch_mala_reverse(const ElemBlock* blocks, int n_blocks, const R* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_mala_accept(int n_chains, const double* S, const double* S_prop,
+cudaError_t launch_mala_accept(int chain0, int n_chains, const double* S, const double* S_prop,
                                const double* qf, const double* qr, const double* log_u,
                                const MalaDev* md, int update_index, int* accept_flag,
                                int* n_accepted, double* log_alpha, cudaStream_t st)
@@ -194,7 +196,8 @@ cudaError_t launch_mala_accept(int n_chains, const double* S, const double* S_pr
     if (n_chains <= 0) return cudaSuccess;
     const int threads = 128;
     mala_accept_kernel<<<(n_chains + threads - 1) / threads, threads, 0, st>>>(
-        n_chains, S, S_prop, qf, qr, log_u, md, update_index, accept_flag, n_accepted, log_alpha);
+        chain0, n_chains, S, S_prop, qf, qr, log_u, md, update_index, accept_flag, n_accepted,
+        log_alpha);
     return cudaGetLastError();
 }
 

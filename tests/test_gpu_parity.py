@@ -309,6 +309,50 @@ def test_host_buffers_match_device_buffers(pamd):
     assert torch.equal(Sp, Sd.cpu()) and torch.equal(gp, gd.cpu())
 
 
+@pytest.mark.parametrize("name,precision,n_updates",
+                         [("ragged", "fp32", 1), ("ragged", "fp64", 2), ("lj500", "fp32", 3),
+                          ("ho3d", "fp32", 2)])
+def test_path_update_host_buffers_match_device_buffers(pamd, name, precision, n_updates):
+    """With host buffers the update is pipelined over chunks of chains (copies of one
+    chunk overlap the updates of another); every chain must come out bit for bit as
+    from one update over device buffers.  The host-side S, acceptance counts and
+    log alpha are covered, and a mix of host and device buffers."""
+    w = inputs.workload(name, "small")
+    paths = start_paths(w, precision)
+    prob = _problem(pamd, w, precision)
+    h = 2e-7 if name != "ho3d" else 1e-5
+    d_pos = _upload(pamd, prob, paths)
+    start = d_pos.cpu()
+    S0, g0 = pamd.action_grad(prob, d_pos)
+    torch.cuda.synchronize()
+    h_pos, h_grad = d_pos.cpu().pin_memory(), g0.cpu().pin_memory()
+    h_S = S0.cpu().pin_memory()
+    h_acc = torch.zeros(prob.n_chains, dtype=torch.int32).pin_memory()
+    h_la = torch.zeros(prob.n_chains, dtype=torch.float64).pin_memory()
+    d_acc = torch.zeros(prob.n_chains, dtype=torch.int32, device="cuda")
+    d_la = torch.zeros(prob.n_chains, dtype=torch.float64, device="cuda")
+    for rep in range(2):
+        pamd.path_update(prob, d_pos, g0, S0, h, n_updates, seed=11, counter=7 + rep,
+                         n_accepted=d_acc, log_alpha=d_la)
+        pamd.path_update(prob, h_pos, h_grad, h_S, h, n_updates, seed=11, counter=7 + rep,
+                         n_accepted=h_acc, log_alpha=h_la)
+    torch.cuda.synchronize()
+    assert int(d_acc.sum()) > 0 and not torch.equal(d_pos.cpu(), start)
+    assert torch.equal(h_pos, d_pos.cpu())
+    assert torch.equal(h_grad, g0.cpu())
+    assert torch.equal(h_S, S0.cpu())
+    assert torch.equal(h_acc, d_acc.cpu())
+    assert torch.equal(h_la, d_la.cpu())
+    # mixed: host path, device gradient cache and counts
+    m_pos = h_pos.clone().pin_memory()
+    m_grad, m_S, m_acc = g0.clone(), S0.clone(), d_acc.clone()
+    pamd.path_update(prob, d_pos, g0, S0, h, 1, seed=12, counter=1, n_accepted=d_acc)
+    pamd.path_update(prob, m_pos, m_grad, m_S, h, 1, seed=12, counter=1, n_accepted=m_acc)
+    torch.cuda.synchronize()
+    assert torch.equal(m_pos, d_pos.cpu())
+    assert torch.equal(m_grad, g0) and torch.equal(m_S, S0) and torch.equal(m_acc, d_acc)
+
+
 def test_autograd_function_and_finite_differences(pamd):
     """PamdAction: backward is the hand-written adjoint; it matches central finite
     differences of the kernel's own action (h = 1e-3, FP64 path) and the oracle."""
