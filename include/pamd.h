@@ -153,7 +153,12 @@ int pamd_action_grad(const pamd_problem* prob, const void* pos, double* S, void*
  *   n_accepted   : int[n_chains_total], incremented by accepted updates (may be NULL).
  *   log_alpha    : double[n_chains_total], log alpha of the last update (may be NULL).
  * With device pointers and n_updates > 1 the updates are captured once into
- * a CUDA graph (cached per shape) and replayed. */
+ * a CUDA graph (cached per shape) and replayed.  With host buffers, no noise
+ * and no log_u, and at least two chains, the call is pipelined over up to 8
+ * chunks of chains: one chunk's buffers are copied in while earlier chunks
+ * are updated and copied back (the library's own streams, ordered after the
+ * work already queued on `stream`); the results are bitwise those of the
+ * device-pointer call, and the call returns once every result is on the host. */
 int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S, double h,
                      int n_updates, uint64_t seed, uint64_t counter, const void* noise,
                      const double* log_u, int* n_accepted, double* log_alpha, void* stream);
