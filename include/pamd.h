@@ -282,10 +282,13 @@ int pamd_device_status(void* stream);
 /* Launch-shape override for the Lennard-Jones kernels (0 or a negative skin
  * keeps the automatic choice): steps per CTA tile, threads per particle
  * (1, 2 or 4), neighbour-list capacity per particle, Verlet skin (sigma
- * units).  Affects plans built afterwards; results do not depend on these
- * (candidate order is fixed), only speed.  Host-side setting, not thread-safe
- * against concurrent calls. */
-int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin);
+ * units; double precision), steps per neighbour-list window (single
+ * precision; >= 2).  Affects plans built afterwards; results do not depend
+ * on these (candidate order is fixed), only speed.  PAMD_ERR_ARG for a
+ * negative size, an unsupported thread count or a window of 1.  Host-side
+ * setting, not thread-safe against concurrent calls. */
+int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin,
+              int window_steps);
 
 /* Harmonic action and gradient that allocates nothing (no counterpart in the
  * paper; it exists for callers, not for the method).

@@ -218,8 +218,9 @@ def normals(seed: int, counter: int, stream_id: int, chain: int, n: int, e0: int
 
 
 def tune(tile_steps: int = 0, threads_per_particle: int = 0, max_neighbours: int = 0,
-         skin: float = -1.0):
-    pamd_tune(tile_steps, threads_per_particle, max_neighbours, skin)
+         skin: float = -1.0, window_steps: int = 0):
+    """Launch-shape override for the LJ kernels (zeros: automatic); see pamd_tune."""
+    pamd_tune(tile_steps, threads_per_particle, max_neighbours, skin, window_steps)
 
 
 def release_cache():

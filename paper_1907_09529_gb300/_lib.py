@@ -96,7 +96,7 @@ def load(path: str = LIB_PATH):
             "pamd_release_cache": (ctypes.c_int, []),
             "pamd_version": (ctypes.c_int, []),
             "pamd_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_double]),
+                                         ctypes.c_double, ctypes.c_int]),
             "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
             "pamd_device_status": (ctypes.c_int, [_VP]),
             "pamd_fragment_mc": (ctypes.c_int, [_PP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -157,8 +157,8 @@ def pamd_normals(seed, counter, stream_id, chain, e0, n, out, stream):
     return _call("pamd_normals", seed, counter, stream_id, chain, e0, n, out, stream)
 
 
-def pamd_tune(tile_steps, threads_per_particle, max_neighbours, skin):
-    return _call("pamd_tune", tile_steps, threads_per_particle, max_neighbours, skin)
+def pamd_tune(tile_steps, threads_per_particle, max_neighbours, skin, window_steps):
+    return _call("pamd_tune", tile_steps, threads_per_particle, max_neighbours, skin, window_steps)
 
 
 def pamd_fragment_mc(prob, pos, l_min, l_max, n_steps, seed, counter, levels, offsets, noise,

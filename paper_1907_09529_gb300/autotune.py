@@ -1,8 +1,9 @@
 """Autotuner for the Lennard-Jones action kernel's launch shape.
 
 For a problem it times ``pamd_action_grad`` (CUDA events, on the current stream)
-over a grid of candidate shapes -- steps per tile, Verlet skin, threads per
-particle, list capacity -- and keeps the fastest.  Results do not depend on the
+over a grid of candidate shapes -- steps per tile, threads per particle, list
+capacity, Verlet skin (double precision), neighbour-list window (single
+precision) -- and keeps the fastest.  Results do not depend on the
 shape (the candidate order inside every sum is fixed), only the speed does, so
 the choice can be cached per problem signature in a small JSON file.
 """
@@ -17,7 +18,7 @@ import torch
 
 from . import Problem, action_grad, tune
 
-Shape = Tuple[int, int, int, float]  # tile_steps, threads_per_particle, max_neighbours, skin
+Shape = Tuple[int, int, int, float, int]  # tile, threads/particle, max neighbours, skin, window
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuned.json")
 
@@ -29,10 +30,10 @@ def signature(p: Problem) -> str:
     return "|".join(parts)
 
 
-def candidates(tiles=(16, 32, 64), tpps=(0,), skins=(0.2, 0.25, 0.3, 0.4),
-               maxnb=(0,)) -> Iterable[Shape]:
-    for t, q, m, s in itertools.product(tiles, tpps, maxnb, skins):
-        yield (t, q, m, s)
+def candidates(tiles=(16, 32, 64), tpps=(0,), skins=(-1.0,), maxnb=(0,),
+               windows=(8, 16, 32)) -> Iterable[Shape]:
+    for t, q, m, s, w in itertools.product(tiles, tpps, maxnb, skins, windows):
+        yield (t, q, m, s, w)
 
 
 def time_shape(p: Problem, pos: torch.Tensor, shape: Shape, reps: int = 3) -> float:
@@ -70,8 +71,8 @@ def autotune(p: Problem, pos: torch.Tensor, shapes: Optional[Iterable[Shape]] = 
         ms = time_shape(p, pos, shape, reps)
         timings[json.dumps(shape)] = ms
         if verbose:
-            print(f"  shape tile={shape[0]} tpp={shape[1]} maxnb={shape[2]} skin={shape[3]}: "
-                  f"{ms:.3f} ms", flush=True)
+            print(f"  shape tile={shape[0]} tpp={shape[1]} maxnb={shape[2]} skin={shape[3]} "
+                  f"window={shape[4]}: {ms:.3f} ms", flush=True)
         if ms < best_ms:
             best, best_ms = shape, ms
     tune(*best)

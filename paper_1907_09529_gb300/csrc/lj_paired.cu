@@ -28,20 +28,18 @@
 // (a, a+1).  An item that does not start at step 0 begins with the pair
 // (t0-1, t0), whose first half only supplies the residual r_{t0-1}.
 //
-// Neighbour lists.  A Verlet list of radius rc + skin, built from the positions
-// at a reference slice, is exact at every slice where no particle is more than
-// skin/2 away from its reference position.  Along a Brownian path the distance
-// from a slice grows like sqrt(|t - t_ref|) on both sides, so a list is built
-// about a reference slice ahead of the current one -- 3/8 of the previous list's
-// lifetime ahead (measured on LJ N=500: 1/2 sits too close to the point where the
-// current pair already fails the test, 1/4 gains less) -- and lasts longer than a
-// list built at the current slice.  If the current pair is not within
-// skin/2 of that reference, the list is rebuilt at the pair's first slice; if one
-// step breaks even that (a path far from Brownian), the pair scans all
+// Neighbour lists.  An item knows every slice it will visit, so its steps are
+// cut into windows of W steps and each window gets a list that is exact for all
+// of its slices: with reference positions x_c at the window's middle slice and
+// delta_i = max over the window's slices of |x_t(i) - x_c(i)| (read from the
+// path), a pair within rc at any slice of the window satisfies
+// |r_ij(x_c)| <= rc + delta_i + delta_j (triangle inequality; the minimum image
+// at x_c is no longer than the image that is within rc at t), so listing those
+// pairs suffices.  A particle whose list would overflow its capacity scans all
 // candidates.  Candidates are visited in increasing j in every case, so each
-// force and Hessian sum runs over the in-cutoff pairs in one fixed order whatever
-// the tiling, skin or list capacity, and the results are bitwise independent of
-// them.
+// force and Hessian sum runs over the in-cutoff pairs in one fixed order
+// whatever the tiling, window or list capacity, and the results are bitwise
+// independent of them.
 #include "pamd_internal.cuh"
 
 namespace pamd {
@@ -90,7 +88,7 @@ struct Smem {
 // Packed constants of one system (built per item from the per-system table).
 struct K2 {
     float2 nL, iL, mag, nmag, c1, c2, c3, duc, m1, m7;
-    float rc2, rl2, hs2, a, ginv;
+    float rc2, rcm, a, ginv;
     __device__ explicit K2(const LJK<float>& k)
     {
         nL = pk(-k.L);
@@ -104,8 +102,7 @@ struct K2 {
         m1 = pk(-1.0f);
         m7 = pk(-7.0f);
         rc2 = k.rc2;
-        rl2 = k.rl2;
-        hs2 = k.hs2;
+        rcm = k.rcm;
         a = k.a;
         ginv = k.ginv;
     }
@@ -170,38 +167,22 @@ struct PairList {
         reinterpret_cast<uint16_t*>(nbr + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
     }
 
-    // Reference position of particle j: slice a of the current pair (AHEAD
-    // false), or the reference slice staged as {x, y, z, 0} in the residual
-    // array (AHEAD true).
-    template <bool AHEAD>
-    __device__ __forceinline__ float3 ref_pos(const Smem<NMAX>& P, int j) const
-    {
-        if (AHEAD) {
-            const float4 v = P.rxy(8 * j);
-            return make_float3(v.x, v.y, v.z);
-        }
-        const float4 v = P.xy(8 * j);
-        return make_float3(v.x, v.z, P.z(8 * j).x);
-    }
-
-    // Verlet list at the reference positions: candidates j = q (mod tpp), two
-    // per packed operation.
-    template <bool AHEAD>
+    // Window list from the reference slice staged as {x, y, z, delta} in the
+    // residual array: candidates j = q (mod tpp), two per packed operation,
+    // listed when r_ij(x_c) <= rc + delta_i + delta_j.
     __device__ void build(const Smem<NMAX>& P, const K2& k)
     {
         cnt = 0;
         ovf = false;
         if (!active) return;
-        const float3 pi = ref_pos<AHEAD>(P, i);
-        xr = pi.x;
-        yr = pi.y;
-        zr = pi.z;
-        const float2 xi = pk(xr), yi = pk(yr), zi = pk(zr);
+        const float4 pi = P.rxy(8 * i);
+        const float2 xi = pk(pi.x), yi = pk(pi.y), zi = pk(pi.z);
+        const float2 ri = pk(k.rcm + pi.w);
         int c = 0;
         for (int j = q; j < N; j += 2 * tpp) {
             const int j2 = j + tpp;
             const int j2c = j2 < N ? j2 : j;
-            const float3 A = ref_pos<AHEAD>(P, j), B = ref_pos<AHEAD>(P, j2c);
+            const float4 A = P.rxy(8 * j), B = P.rxy(8 * j2c);
             float2 dx = sub2(xi, pk(A.x, B.x));
             float2 dy = sub2(yi, pk(A.y, B.y));
             float2 dz = sub2(zi, pk(A.z, B.z));
@@ -209,11 +190,13 @@ struct PairList {
             dy = fma2(k.nL, add2(fma2(dy, k.iL, k.mag), k.nmag), dy);
             dz = fma2(k.nL, add2(fma2(dz, k.iL, k.mag), k.nmag), dz);
             const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-            if (j != i && r2.x <= k.rl2) {
+            const float2 lim = add2(ri, pk(A.w, B.w));
+            const float2 lim2 = mul2(lim, lim);
+            if (j != i && r2.x <= lim2.x) {
                 if (c < cap) put(c, 8 * j);
                 ++c;
             }
-            if (j2 < N && j2 != i && r2.y <= k.rl2) {
+            if (j2 < N && j2 != i && r2.y <= lim2.y) {
                 if (c < cap) put(c, 8 * j2);
                 ++c;
             }
@@ -222,26 +205,12 @@ struct PairList {
         ovf = c > cap;
     }
 
-    // Has particle i left the skin/2 ball around its build position at slice a
-    // (first) or b (second)?
-    __device__ void moved(const Smem<NMAX>& P, const K2& k, bool& ma, bool& mb) const
-    {
-        ma = mb = false;
-        if (!active) return;
-        const float4 pxy = P.xy(8 * i);
-        const float2 pz = P.z(8 * i);
-        const float ax = pxy.x - xr, ay = pxy.z - yr, az = pz.x - zr;
-        const float bx = pxy.y - xr, by = pxy.w - yr, bz = pz.y - zr;
-        ma = ax * ax + ay * ay + az * az > k.hs2;
-        mb = bx * bx + by * by + bz * bz > k.hs2;
-    }
-
     // Calls f(8 j) for the candidates j of particle i, in increasing j.
     template <typename F>
-    __device__ __forceinline__ void for_each_candidate(bool scan_all, F&& f) const
+    __device__ __forceinline__ void for_each_candidate(F&& f) const
     {
         if (!active) return;
-        if (!ovf && !scan_all) {
+        if (!ovf) {
             const uint32_t* w = nbr + tid;
             int m = 0;
             for (; m + 1 < cnt; m += 2, w += NT) {
@@ -266,14 +235,13 @@ struct PairList {
     }
 
     // F(x_a), F(x_b) of particle i (complete in every thread of the group).
-    __device__ void force(const Smem<NMAX>& P, const K2& k, bool scan_all, float2& fx, float2& fy,
-                          float2& fz) const
+    __device__ void force(const Smem<NMAX>& P, const K2& k, float2& fx, float2& fy, float2& fz) const
     {
         fx = fy = fz = pk(0.0f);
         if (active) {
             const float4 pxy = P.xy(8 * i);
             const float2 xi = pk(pxy.x, pxy.y), yi = pk(pxy.z, pxy.w), zi = P.z(8 * i);
-            for_each_candidate(scan_all, [&](int o8) {
+            for_each_candidate([&](int o8) {
                 float2 dx, dy, dz, w, ir2, ir6;
                 const float2 r2 = pair_geom(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
                 const float2 fs = pair_fs(r2, k, w, ir2, ir6);
@@ -287,13 +255,13 @@ struct PairList {
 
     // (H(x_a) v_a, H(x_b) v_b) of particle i; v is the residual array, vi its own value.
     __device__ void hvp(const Smem<NMAX>& P, float2 vix, float2 viy, float2 viz, const K2& k,
-                        bool scan_all, float2& hx, float2& hy, float2& hz) const
+                        float2& hx, float2& hy, float2& hz) const
     {
         hx = hy = hz = pk(0.0f);
         if (active) {
             const float4 pxy = P.xy(8 * i);
             const float2 xi = pk(pxy.x, pxy.y), yi = pk(pxy.z, pxy.w), zi = P.z(8 * i);
-            for_each_candidate(scan_all, [&](int o8) {
+            for_each_candidate([&](int o8) {
                 float2 dx, dy, dz, w, ir2, ir6;
                 const float2 r2 = pair_geom(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
                 const float2 fs = pair_fs(r2, k, w, ir2, ir6);                       // -U'/r
@@ -319,13 +287,11 @@ __device__ __forceinline__ float sq3(float x, float y, float z)
 }
 
 // One work item: steps [t0, t1) of one chain.
-// ahead: how many steps past the current pair the next list's reference slice
-// lies (carried from item to item; adapted to the observed list lifetime).
 template <bool GRAD, int NMAX>
 __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<float>& S,
                                             unsigned char* smem, const float* __restrict__ pos,
                                             float* __restrict__ grad, double* __restrict__ partials,
-                                            double* red, int& ahead)
+                                            double* red)
 {
     const int N = S.N;
     const Smem<NMAX> P{smem};
@@ -365,8 +331,8 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
 
     float rpx = 0.0f, rpy = 0.0f, rpz = 0.0f;  // r_{a-1}
     double acc = 0.0;
-    bool built = false;
-    int a_built = ts;  // first slice of the pair at which the current list was built
+    const int W = max(2, S.window);
+    int win_end = ts;  // slices [.., win_end) are covered by the current list
 
     for (int a = ts; a < t1; a += 2) {
         const int b = a + 1;
@@ -384,38 +350,31 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
             zn = __ldg(Xb1 + 2 * N);
         }
 
-        // Neighbour list valid for both slices?
-        bool ma, mb;
-        L.moved(P, k, ma, mb);
-        bool scan_all = false;
-        if (__syncthreads_or(!built || ma || mb)) {
-            if (built) ahead = max(1, min(64, (3 * (a - a_built)) / 8));
-            const int c = min(a + ahead, t1);  // reference slice (c <= T)
-            bool ok = false;
-            if (c > b) {
-                // Stage slice c as {x, y, z, 0} in the residual array (free until
-                // the residuals of this pair are written, after the next barrier).
-                for (int n = threadIdx.x; n < N; n += blockDim.x) {
-                    const float* A = X + (long long)c * s + n;
-                    P.rxy(8 * n) = make_float4(__ldg(A), __ldg(A + N), __ldg(A + 2 * N), 0.0f);
+        if (b >= win_end) {
+            // New window: slices [a, e) (every pair inside has b <= t1 <= T).
+            const int e = min(a + W, t1 + 1), c = a + (e - 1 - a) / 2;
+            for (int n = threadIdx.x; n < N; n += blockDim.x) {
+                const float* A = X + n;
+                const float* C = A + (long long)c * s;
+                const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
+                float d2 = 0.0f;
+                for (int t = a; t < e; ++t) {
+                    const float* Q = A + (long long)t * s;
+                    const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
+                    d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
                 }
-                __syncthreads();
-                L.template build<true>(P, k);
-                L.moved(P, k, ma, mb);
-                ok = !__syncthreads_or(ma || mb);
+                // delta rounded up: sqrt and the sums above are within a few ulp
+                const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
+                P.rxy(8 * n) = make_float4(cx, cy, cz, delta);
             }
-            if (!ok) {
-                L.template build<false>(P, k);
-                L.moved(P, k, ma, mb);
-                scan_all = __syncthreads_or(mb);
-                ahead = 1;
-            }
-            built = true;
-            a_built = a;
+            __syncthreads();
+            L.build(P, k);
+            __syncthreads();  // the staged reference is overwritten by residuals below
+            win_end = e;
         }
 
         float2 fx, fy, fz;
-        L.force(P, k, scan_all, fx, fy, fz);
+        L.force(P, k, fx, fy, fz);
         float2 rx = pk(0.0f), ry = pk(0.0f), rz = pk(0.0f);
         if (L.active) {
             const float4 pxy = P.xy(8 * i);
@@ -437,7 +396,7 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
         if (GRAD) {
             __syncthreads();
             float2 hx, hy, hz;
-            L.hvp(P, rx, ry, rz, k, scan_all, hx, hy, hz);
+            L.hvp(P, rx, ry, rz, k, hx, hy, hz);
             if (lead) {
                 // g = (r_prev - r + a H r) / (2 D dt), packed over (a, b).
                 const float2 gx = mul2(fma2(pk(k.a), hx, sub2(pk(rpx, rx.x), rx)), ginv);
@@ -486,7 +445,6 @@ __global__ void __launch_bounds__(MAXT, 1)
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ int s_item;
-    int ahead = 4;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -495,7 +453,7 @@ __global__ void __launch_bounds__(MAXT, 1)
         if (it >= n_items) break;
         const LJItem I = items[it];
         const LJSysDev<float> S = systems[I.sys];
-        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red, ahead);
+        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red);
     }
 }
 

@@ -39,6 +39,7 @@ struct NvtxRange {
 struct LJTune {
     int tile_steps = 0, tpp = 0, maxnb = 0;
     double skin = -1.0;
+    int window = 0;  // paired kernel: steps per neighbour-list window
 };
 
 LJTune g_tune_override;  // 0 / negative fields mean "automatic"
@@ -213,7 +214,8 @@ std::string plan_key(const pamd_problem* p)
     os.precision(17);
     os << p->precision << '|' << p->flags << '|' << p->D << ',' << p->beta << ',' << p->dt << '|'
        << p->n_systems << '|' << g_tune_override.tile_steps
-       << ',' << g_tune_override.tpp << ',' << g_tune_override.maxnb << ',' << g_tune_override.skin;
+       << ',' << g_tune_override.tpp << ',' << g_tune_override.maxnb << ',' << g_tune_override.skin
+       << ',' << g_tune_override.window;
     for (int q = 0; q < p->n_systems; ++q) {
         const pamd_system& s = p->systems[q];
         os << '|' << s.n_particles << ',' << s.n_steps << ',' << s.dim << ',' << s.n_chains << ','
@@ -245,8 +247,10 @@ int choose_lj_block(const pamd_problem* p)
 }
 
 // Per-system LJ launch shape: threads per particle (largest power of two <= 8
-// with N * tpp <= NT), Verlet skin, list capacity per thread, tile length.
-LJTune choose_lj_tune(const pamd_system& s, int NT, int cap_lane_max)
+// with N * tpp <= NT), Verlet skin (one-step kernel) or window length (paired
+// kernel), list capacity per thread, tile length.  sig_step = sqrt(2 D dt), the
+// per-component spread of one Brownian step.
+LJTune choose_lj_tune(const pamd_system& s, int NT, int cap_lane_max, bool paired, double sig_step)
 {
     LJTune t;
     const int N = s.n_particles;
@@ -261,7 +265,15 @@ LJTune choose_lj_tune(const pamd_system& s, int NT, int cap_lane_max)
     t.tpp = tpp;
     t.skin = g_tune_override.skin >= 0 ? g_tune_override.skin : 0.3;
     t.tile_steps = g_tune_override.tile_steps > 0 ? g_tune_override.tile_steps : 32;
-    const double L = s.pot.box, rho = N / (L * L * L), rl = s.pot.rc + t.skin;
+    t.window = g_tune_override.window > 0 ? g_tune_override.window : 16;
+    double rl = s.pot.rc + t.skin;
+    if (paired) {
+        // Window lists reach rc + delta_i + delta_j; size them for margins of about
+        // 3.5 times the spread of a 3D displacement over half a window.
+        const double dmax = 3.5 * sig_step * std::sqrt(3.0 * 0.5 * t.window);
+        rl = s.pot.rc + 2.0 * dmax;
+    }
+    const double L = s.pot.box, rho = N / (L * L * L);
     const double expect = 4.18879020478639 * rl * rl * rl * rho;  // 4/3 pi rl^3 rho
     int want = (int)(1.2 * expect) + 8;
     if (want > N - 1 + tpp) want = N - 1 + tpp;
@@ -289,6 +301,7 @@ void fill_lj_sys(Plan* P, const pamd_problem* p)
         d.lg_tpp = 0;
         while ((1 << d.lg_tpp) < d.tpp) ++d.lg_tpp;
         d.cap = si.tune.maxnb;
+        d.window = si.tune.window;
         LJConst c;
         c.L = si.pot.box;
         c.rc = si.pot.rc;
@@ -403,7 +416,8 @@ int build_plan(const pamd_problem* p, Plan** out)
             for (int q = 0; q < (int)P->sys.size(); ++q) {
                 SysInfo& si = P->sys[q];
                 if (si.kind != PAMD_LJ) continue;
-                si.tune = choose_lj_tune(p->systems[q], NT, cap_lane_max);
+                si.tune = choose_lj_tune(p->systems[q], NT, cap_lane_max, P->lj_paired,
+                                         std::sqrt(2.0 * p->D * p->dt));
                 cap_used = std::max(cap_used, si.tune.maxnb);
                 si.n_tiles = (si.T + si.tune.tile_steps - 1) / si.tune.tile_steps;
                 si.slot0 = slot;
@@ -791,17 +805,20 @@ int pamd_device_status(void* stream)
     return worst;
 }
 
-int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin)
+int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin,
+              int window_steps)
 {
     if (threads_per_particle != 0 && threads_per_particle != 1 && threads_per_particle != 2 &&
         threads_per_particle != 4)
         return PAMD_ERR_ARG;
-    if (tile_steps < 0 || max_neighbours < 0) return PAMD_ERR_ARG;
+    if (tile_steps < 0 || max_neighbours < 0 || window_steps < 0 || window_steps == 1)
+        return PAMD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mutex);
     g_tune_override.tile_steps = tile_steps;
     g_tune_override.tpp = threads_per_particle;
     g_tune_override.maxnb = max_neighbours;
     g_tune_override.skin = skin;
+    g_tune_override.window = window_steps;
     return PAMD_OK;
 }
 

@@ -189,6 +189,7 @@ struct LJConst {
 template <typename R>
 struct LJK {
     R L, iL, rc2, rl2, hs2;  // box, 1/box, rc^2, list radius^2, (skin/2)^2
+    R rcm;                   // rc plus a margin that covers rounding in window lists
     R c1, c2, c3, duc;       // 24 eps sigma^6, 2 sigma^6, 26 sigma^6, u'(rc)
     R a, ginv, sig_em;       // beta D dt, 1/(2 D dt), sqrt(2 D dt)
 };
@@ -216,6 +217,7 @@ inline LJK<R> make_lj_consts(const LJConst& c, double sig_em)
         k.rc2 = (R)(c.rc * c.rc);
     }
     k.rl2 = (R)(rl * rl);
+    k.rcm = (R)(c.rc * (1.0 + 1.0e-6) + 1.0e-5);
     k.hs2 = (R)(0.25 * c.skin * c.skin);
     k.c1 = (R)(24.0 * c.eps * s6);
     k.c2 = (R)(2.0 * s6);
@@ -235,6 +237,7 @@ struct LJSysDev {
     int N, T;
     int tpp, lg_tpp;      // threads per particle (power of two) and its log2
     int cap;              // neighbour-list capacity per thread
+    int window;           // steps per neighbour-list window (paired kernel)
     LJK<R> k;
 };
 

@@ -119,16 +119,16 @@ def test_edge_cases_tiny_paths(pamd):
 @pytest.mark.parametrize("name", ["lj108", "lj500"])
 def test_results_independent_of_tiling(pamd, name):
     """Candidate order is fixed, so S and the gradient are bitwise the same for any
-    tile, skin (including skins small enough that single steps fall back to the
-    all-candidate scan) and list capacity (including the overflow path).  In
-    lj108's box rc + skin exceeds L/2; in lj500's it does not."""
+    tile, neighbour-list window (down to one list per step pair) and list
+    capacity (including the overflow path, where a particle scans every
+    candidate).  In lj108's box the lists reach past L/2; in lj500's they do not."""
     w = inputs.workload(name, "small")
     paths = start_paths(w, "fp32")
     outs = []
     try:
-        for tile, tpp, maxnb, skin in [(32, 0, 0, -1), (1, 0, 0, -1), (7, 0, 0, 0.05),
-                                       (64, 0, 0, 0.6), (16, 0, 8, -1)]:
-            pamd.tune(tile, tpp, maxnb, skin)
+        for tile, tpp, maxnb, window in [(32, 0, 0, 0), (1, 0, 0, 0), (7, 0, 0, 2),
+                                         (64, 0, 0, 40), (16, 0, 8, 0), (33, 0, 0, 5)]:
+            pamd.tune(tile, tpp, maxnb, -1.0, window)
             prob = _problem(pamd, w, "fp32")
             buf = _upload(pamd, prob, paths)
             S, g = pamd.action_grad(prob, buf)
