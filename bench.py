@@ -475,6 +475,31 @@ def main():
     ms_max = max_over_ranks(ms, dev)
     value = aggregate(units_rank, world, args.steps, ms_max)
 
+    # End to end through the C ABI with host buffers (right after the timed steps,
+    # before the long plain-FP64 leg): every step copies the path,
+    # its cached gradient and action to the device and the updated ones back.
+    e2e = None
+    if not args.no_e2e:
+        hpos = pos.cpu().pin_memory()
+        hgrad = grad.cpu().pin_memory()
+        hS = S.cpu().pin_memory()
+        hacc = torch.zeros(prob.n_chains, dtype=torch.int32).pin_memory()
+        pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=5, n_accepted=hacc)
+        ne = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        e2e_clocks = ClockSampler(local)
+        e2e_clocks.start()
+        t0 = time.perf_counter()
+        for i in range(ne):
+            pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=6 + i, n_accepted=hacc)
+        t_e2e = (time.perf_counter() - t0) / ne
+        e2e_clk = e2e_clocks.stop()
+        nbuf = prob.span * 4
+        e2e = {"value": units_rank * world / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
+               "d2h_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
+               "ms_per_step": t_e2e * 1e3, "sm_mhz": e2e_clk.get("sm_mhz")}
+
     # Dominant kernel: the action + adjoint kernel alone (one launch per LJ system
     # + a tiny finalize), timed with events on its stream over the same data.
     nk = 10
@@ -545,27 +570,6 @@ def main():
                  "speedup_batched_vs_plain": ms64 / ms_kernel,
                  "fp32_vs_fp64_rel_err_S": relS, "fp32_vs_fp64_rel_err_grad": relG}
         del pos64, S64, g64
-
-    # End to end through the C ABI with host buffers: every step copies the path,
-    # its cached gradient and action to the device and the updated ones back.
-    e2e = None
-    if not args.no_e2e:
-        hpos = pos.cpu().pin_memory()
-        hgrad = grad.cpu().pin_memory()
-        hS = S.cpu().pin_memory()
-        hacc = torch.zeros(prob.n_chains, dtype=torch.int32).pin_memory()
-        pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=5, n_accepted=hacc)
-        ne = max(3, min(args.steps, 10))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(ne):
-            pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=6 + i, n_accepted=hacc)
-        t_e2e = (time.perf_counter() - t0) / ne
-        nbuf = prob.span * 4
-        e2e = {"value": units_rank * world / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
-               "d2h_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
-               "ms_per_step": t_e2e * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -265,7 +265,7 @@ LJTune choose_lj_tune(const pamd_system& s, int NT, int cap_lane_max, bool paire
     t.tpp = tpp;
     t.skin = g_tune_override.skin >= 0 ? g_tune_override.skin : 0.3;
     t.tile_steps = g_tune_override.tile_steps > 0 ? g_tune_override.tile_steps : 32;
-    t.window = g_tune_override.window > 0 ? g_tune_override.window : 16;
+    t.window = g_tune_override.window > 0 ? g_tune_override.window : 24;
     double rl = s.pot.rc + t.skin;
     if (paired) {
         // Window lists reach rc + delta_i + delta_j; size them for margins of about
