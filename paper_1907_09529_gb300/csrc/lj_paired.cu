@@ -35,8 +35,12 @@
 // path), a pair within rc at any slice of the window satisfies
 // |r_ij(x_c)| <= rc + delta_i + delta_j (triangle inequality; the minimum image
 // at x_c is no longer than the image that is within rc at t), so listing those
-// pairs suffices.  A particle whose list would overflow its capacity scans all
-// candidates.  Candidates are visited in increasing j in every case, so each
+// pairs suffices.  The window lists are built from an outer list made once per
+// item by the same rule with item-wide margins (reference at the item's middle
+// slice), which holds every pair that any of the item's windows can need; it
+// sits in global memory (one region per CTA, L2-resident).  A particle whose
+// outer list overflows builds its window lists from all candidates; one whose
+// window list overflows scans all candidates.  Candidates are visited in increasing j in every case, so each
 // force and Hessian sum runs over the in-cutoff pairs in one fixed order
 // whatever the tiling, window or list capacity, and the results are bitwise
 // independent of them.
@@ -141,13 +145,18 @@ __device__ __forceinline__ float2 pair_fs(float2 r2, const K2& k, float2& w, flo
 // The particle a thread works for, its list, and the candidate loop.
 template <int NMAX>
 struct PairList {
-    int N, NT, tid, i, q, tpp, cap, cnt;
-    bool active, ovf;
+    int N, NT, tid, i, q, tpp, cap, cnt, ocap, ocnt;
+    bool active, ovf, oovf;
     uint32_t* nbr;
-    float xr, yr, zr;
+    uint32_t* outer;  // this CTA's outer lists (global memory), same word layout
 
-    __device__ void init(int n, int tpp_, int lg, int cap_, uint32_t* list)
+    __device__ void init(int n, int tpp_, int lg, int cap_, uint32_t* list, int ocap_,
+                         uint32_t* outer_)
     {
+        ocap = ocap_ & ~1;
+        outer = outer_;
+        ocnt = 0;
+        oovf = true;
         N = n;
         NT = blockDim.x;
         tid = threadIdx.x;
@@ -167,38 +176,88 @@ struct PairList {
         reinterpret_cast<uint16_t*>(nbr + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
     }
 
-    // Window list from the reference slice staged as {x, y, z, delta} in the
-    // residual array: candidates j = q (mod tpp), two per packed operation,
-    // listed when r_ij(x_c) <= rc + delta_i + delta_j.
+    // Pair test at the staged reference {x, y, z, delta} (residual array) of
+    // two candidates: r_ij(x_c) <= rc + delta_i + delta_j for each half.
+    __device__ __forceinline__ void test2(const Smem<NMAX>& P, const K2& k, float4 pi, int o1,
+                                          int o2, bool& in1, bool& in2) const
+    {
+        const float4 A = P.rxy(o1), B = P.rxy(o2);
+        float2 dx = sub2(pk(pi.x), pk(A.x, B.x));
+        float2 dy = sub2(pk(pi.y), pk(A.y, B.y));
+        float2 dz = sub2(pk(pi.z), pk(A.z, B.z));
+        dx = fma2(k.nL, add2(fma2(dx, k.iL, k.mag), k.nmag), dx);
+        dy = fma2(k.nL, add2(fma2(dy, k.iL, k.mag), k.nmag), dy);
+        dz = fma2(k.nL, add2(fma2(dz, k.iL, k.mag), k.nmag), dz);
+        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float2 lim = add2(pk(k.rcm + pi.w), pk(A.w, B.w));
+        const float2 lim2 = mul2(lim, lim);
+        in1 = r2.x <= lim2.x;
+        in2 = r2.y <= lim2.y;
+    }
+
+    // Outer list of the item (reference and item-wide margins staged): all
+    // candidates j = q (mod tpp), in increasing j.
+    __device__ void build_outer(const Smem<NMAX>& P, const K2& k)
+    {
+        ocnt = 0;
+        oovf = true;
+        if (!active) return;
+        const float4 pi = P.rxy(8 * i);
+        int c = 0;
+        auto add = [&](bool in, int o8) {
+            if (in) {
+                if (c < ocap)
+                    reinterpret_cast<uint16_t*>(outer + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
+                ++c;
+            }
+        };
+        for (int j = q; j < N; j += 2 * tpp) {
+            const int j2 = j + tpp;
+            const int j2c = j2 < N ? j2 : j;
+            bool in1, in2;
+            test2(P, k, pi, 8 * j, 8 * j2c, in1, in2);
+            add(j != i && in1, 8 * j);
+            add(j2 < N && j2 != i && in2, 8 * j2);
+        }
+        ocnt = c;
+        oovf = c > ocap;
+    }
+
+    // Window list (window reference and margins staged) from the outer list,
+    // or from all candidates if the outer list overflowed; increasing j.
     __device__ void build(const Smem<NMAX>& P, const K2& k)
     {
         cnt = 0;
         ovf = false;
         if (!active) return;
         const float4 pi = P.rxy(8 * i);
-        const float2 xi = pk(pi.x), yi = pk(pi.y), zi = pk(pi.z);
-        const float2 ri = pk(k.rcm + pi.w);
         int c = 0;
-        for (int j = q; j < N; j += 2 * tpp) {
-            const int j2 = j + tpp;
-            const int j2c = j2 < N ? j2 : j;
-            const float4 A = P.rxy(8 * j), B = P.rxy(8 * j2c);
-            float2 dx = sub2(xi, pk(A.x, B.x));
-            float2 dy = sub2(yi, pk(A.y, B.y));
-            float2 dz = sub2(zi, pk(A.z, B.z));
-            dx = fma2(k.nL, add2(fma2(dx, k.iL, k.mag), k.nmag), dx);
-            dy = fma2(k.nL, add2(fma2(dy, k.iL, k.mag), k.nmag), dy);
-            dz = fma2(k.nL, add2(fma2(dz, k.iL, k.mag), k.nmag), dz);
-            const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-            const float2 lim = add2(ri, pk(A.w, B.w));
-            const float2 lim2 = mul2(lim, lim);
-            if (j != i && r2.x <= lim2.x) {
-                if (c < cap) put(c, 8 * j);
+        auto add = [&](bool in, int o8) {
+            if (in) {
+                if (c < cap) put(c, o8);
                 ++c;
             }
-            if (j2 < N && j2 != i && r2.y <= lim2.y) {
-                if (c < cap) put(c, 8 * j2);
-                ++c;
+        };
+        if (!oovf) {
+            const uint32_t* w = outer + tid;
+            for (int m = 0; m < ocnt; m += 2, w += NT) {
+                const uint32_t v = *w;
+                const int o1 = (int)(v & 0xFFFFu);
+                const bool two = m + 1 < ocnt;
+                const int o2 = two ? (int)(v >> 16) : o1;
+                bool in1, in2;
+                test2(P, k, pi, o1, o2, in1, in2);
+                add(in1, o1);
+                add(two && in2, o2);
+            }
+        } else {
+            for (int j = q; j < N; j += 2 * tpp) {
+                const int j2 = j + tpp;
+                const int j2c = j2 < N ? j2 : j;
+                bool in1, in2;
+                test2(P, k, pi, 8 * j, 8 * j2c, in1, in2);
+                add(j != i && in1, 8 * j);
+                add(j2 < N && j2 != i && in2, 8 * j2);
             }
         }
         cnt = c;
@@ -291,12 +350,12 @@ template <bool GRAD, int NMAX>
 __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<float>& S,
                                             unsigned char* smem, const float* __restrict__ pos,
                                             float* __restrict__ grad, double* __restrict__ partials,
-                                            double* red)
+                                            double* red, uint32_t* outer)
 {
     const int N = S.N;
     const Smem<NMAX> P{smem};
     PairList<NMAX> L;
-    L.init(N, S.tpp, S.lg_tpp, S.cap, P.list());
+    L.init(N, S.tpp, S.lg_tpp, S.cap, P.list(), S.outer_cap, outer);
     const K2 k(S.k);
     const float2 na = pk(-k.a), ginv = pk(k.ginv);
 
@@ -329,6 +388,27 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
     }
     __syncthreads();
 
+    // Stage the reference of slices [lo, hi) -- the middle slice -- with each
+    // particle's margin delta = max |x_t - x_c| over them, as {x, y, z, delta}.
+    auto stage = [&](int lo, int hi) {
+        const int c = lo + (hi - 1 - lo) / 2;
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            const float* A = X + n;
+            const float* C = A + (long long)c * s;
+            const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
+            float d2 = 0.0f;
+#pragma unroll 4
+            for (int t = lo; t < hi; ++t) {
+                const float* Q = A + (long long)t * s;
+                const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
+                d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
+            }
+            // delta rounded up: sqrt and the sums above are within a few ulp
+            const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
+            P.rxy(8 * n) = make_float4(cx, cy, cz, delta);
+        }
+    };
+
     float rpx = 0.0f, rpy = 0.0f, rpz = 0.0f;  // r_{a-1}
     double acc = 0.0;
     const int W = max(2, S.window);
@@ -350,23 +430,17 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
             zn = __ldg(Xb1 + 2 * N);
         }
 
+        if (a == ts) {
+            // Outer list over the item's slices [ts, t1].
+            stage(ts, t1 + 1);
+            __syncthreads();
+            L.build_outer(P, k);
+            __syncthreads();  // the staged reference is replaced below
+        }
         if (b >= win_end) {
             // New window: slices [a, e) (every pair inside has b <= t1 <= T).
-            const int e = min(a + W, t1 + 1), c = a + (e - 1 - a) / 2;
-            for (int n = threadIdx.x; n < N; n += blockDim.x) {
-                const float* A = X + n;
-                const float* C = A + (long long)c * s;
-                const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
-                float d2 = 0.0f;
-                for (int t = a; t < e; ++t) {
-                    const float* Q = A + (long long)t * s;
-                    const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
-                    d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
-                }
-                // delta rounded up: sqrt and the sums above are within a few ulp
-                const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
-                P.rxy(8 * n) = make_float4(cx, cy, cz, delta);
-            }
+            const int e = min(a + W, t1 + 1);
+            stage(a, e);
             __syncthreads();
             L.build(P, k);
             __syncthreads();  // the staged reference is overwritten by residuals below
@@ -440,7 +514,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     lj_paired_kernel(const LJItem* __restrict__ items, int n_items,
                      const LJSysDev<float>* __restrict__ systems, const float* __restrict__ pos,
                      float* __restrict__ grad, double* __restrict__ partials,
-                     int* __restrict__ counter)
+                     int* __restrict__ counter, uint32_t* __restrict__ outer, long long outer_words)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double red[32];
@@ -453,7 +527,8 @@ __global__ void __launch_bounds__(MAXT, 1)
         if (it >= n_items) break;
         const LJItem I = items[it];
         const LJSysDev<float> S = systems[I.sys];
-        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red);
+        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red,
+                                outer + (long long)blockIdx.x * outer_words);
     }
 }
 
@@ -484,7 +559,8 @@ int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad)
 
 cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
                              const float* pos, float* grad, double* partials, int* counter, int NT,
-                             size_t smem, int grid, bool with_grad, cudaStream_t st)
+                             size_t smem, int grid, bool with_grad, uint32_t* outer,
+                             long long outer_words, cudaStream_t st)
 {
     if (n_items <= 0) return cudaSuccess;
     if (NT > 1024) return cudaErrorInvalidValue;
@@ -494,7 +570,7 @@ cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_t
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, smem, st>>>(items, n_items, static_cast<const LJSysDev<float>*>(sys_table),
-                                 pos, grad, partials, counter);
+                                 pos, grad, partials, counter, outer, outer_words);
     return cudaGetLastError();
 }
 

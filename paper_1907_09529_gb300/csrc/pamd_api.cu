@@ -39,7 +39,8 @@ struct NvtxRange {
 struct LJTune {
     int tile_steps = 0, tpp = 0, maxnb = 0;
     double skin = -1.0;
-    int window = 0;  // paired kernel: steps per neighbour-list window
+    int window = 0;     // paired kernel: steps per neighbour-list window
+    int outer_cap = 0;  // paired kernel: outer-list entries per thread
 };
 
 LJTune g_tune_override;  // 0 / negative fields mean "automatic"
@@ -119,6 +120,9 @@ struct Plan {
     int* d_stage_int = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::vector<void*> allocs;
+    // paired LJ kernel: outer lists, two sets (compute lanes) of one region per CTA
+    uint32_t* d_outer = nullptr;
+    long long outer_words = 0;  // 32-bit words per CTA region
     // host-buffer pipeline: copy streams, a second compute stream, events and one LJ
     // work counter per chunk (created on first use)
     cudaStream_t s_in = nullptr, s_out = nullptr, s_cmp = nullptr;
@@ -265,7 +269,7 @@ LJTune choose_lj_tune(const pamd_system& s, int NT, int cap_lane_max, bool paire
     t.tpp = tpp;
     t.skin = g_tune_override.skin >= 0 ? g_tune_override.skin : 0.3;
     t.tile_steps = g_tune_override.tile_steps > 0 ? g_tune_override.tile_steps : 32;
-    t.window = g_tune_override.window > 0 ? g_tune_override.window : 24;
+    t.window = g_tune_override.window > 0 ? g_tune_override.window : 12;
     double rl = s.pot.rc + t.skin;
     if (paired) {
         // Window lists reach rc + delta_i + delta_j; size them for margins of about
@@ -274,6 +278,16 @@ LJTune choose_lj_tune(const pamd_system& s, int NT, int cap_lane_max, bool paire
         rl = s.pot.rc + 2.0 * dmax;
     }
     const double L = s.pot.box, rho = N / (L * L * L);
+    if (paired) {
+        // Outer lists reach rc + Delta_i + Delta_j with item-wide margins; size them
+        // for about 2.5 times the spread of a 3D displacement over half a tile (a
+        // particle beyond that builds its window lists from every candidate).
+        const double dmax = 2.5 * sig_step * std::sqrt(3.0 * 0.5 * (t.tile_steps + 1));
+        const double ro = s.pot.rc + 2.0 * dmax;
+        int ow = (int)(1.2 * 4.18879020478639 * ro * ro * ro * rho) + 16;
+        ow = std::min(ow, N - 1 + 2 * tpp);
+        t.outer_cap = std::max(2, std::min((ow + tpp - 1) / tpp, kMaxListPerThread)) & ~1;
+    }
     const double expect = 4.18879020478639 * rl * rl * rl * rho;  // 4/3 pi rl^3 rho
     int want = (int)(1.2 * expect) + 8;
     if (want > N - 1 + tpp) want = N - 1 + tpp;
@@ -302,6 +316,7 @@ void fill_lj_sys(Plan* P, const pamd_problem* p)
         while ((1 << d.lg_tpp) < d.tpp) ++d.lg_tpp;
         d.cap = si.tune.maxnb;
         d.window = si.tune.window;
+        d.outer_cap = si.tune.outer_cap;
         LJConst c;
         c.L = si.pot.box;
         c.rc = si.pot.rc;
@@ -324,6 +339,7 @@ int build_plan(const pamd_problem* p, Plan** out)
         return PAMD_OK;
     }
     std::unique_ptr<Plan> P(new Plan());
+    int rc0;
     P->key = key;
     P->fp64 = p->precision == PAMD_FP64;
     P->esz = P->fp64 ? 8 : 4;
@@ -476,6 +492,15 @@ int build_plan(const pamd_problem* p, Plan** out)
             if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
             P->lj_grid_grad = std::max(1, std::min((int)items.size(), bg * sms));
             P->lj_grid_nograd = std::max(1, std::min((int)items.size(), bn * sms));
+            if (P->lj_paired) {
+                int ocap = 2;
+                for (auto& si : P->sys)
+                    if (si.kind == PAMD_LJ) ocap = std::max(ocap, si.tune.outer_cap);
+                P->outer_words = (long long)(ocap / 2) * NT;
+                const long long grid = std::max(P->lj_grid_grad, P->lj_grid_nograd);
+                if ((rc0 = P->alloc(&P->d_outer, sizeof(uint32_t) * 2 * grid * P->outer_words)))
+                    return rc0;
+            }
             if (P->fp64)
                 fill_lj_sys<double>(P.get(), p);
             else
@@ -567,7 +592,7 @@ bool is_host_ptr(const void* ptr)
 // depend on the range it is computed in.
 template <typename R>
 int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_out, bool with_grad,
-               cudaStream_t st, int c0 = 0, int c1 = -1, int* counter = nullptr)
+               cudaStream_t st, int c0 = 0, int c1 = -1, int* counter = nullptr, int lane = 0)
 {
     if (c1 < 0) c1 = P->n_chains;
     if (!counter) counter = P->d_counter;  // LJ work-queue counter of this launch sequence
@@ -605,9 +630,12 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
         const int grid = with_grad ? P->lj_grid_grad : P->lj_grid_nograd;
         auto launch = [&](const LJItem* items, int n, int g) {
             if (std::is_same<R, float>::value && P->lj_paired)
-                return launch_lj_paired(items, n, P->d_lj_sys, (const float*)pos,
-                                        (float*)grad, P->d_part_S, counter, P->lj_NT, P->lj_smem,
-                                        g, with_grad, st);
+                return launch_lj_paired(
+                    items, n, P->d_lj_sys, (const float*)pos, (float*)grad, P->d_part_S, counter,
+                    P->lj_NT, P->lj_smem, g, with_grad,
+                    P->d_outer + (long long)lane * std::max(P->lj_grid_grad, P->lj_grid_nograd) *
+                                     P->outer_words,
+                    P->outer_words, st);
             return launch_lj_items<R>(items, n, P->d_lj_sys, P->lj_nmax, pos, grad, P->d_part_S,
                                       counter, P->lj_NT, P->lj_smem, g, with_grad, st);
         };
@@ -635,7 +663,7 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
 template <typename R>
 int run_one_update(const pamd_problem* p, Plan* P, R* pos, R* grad, double* S, const R* noise,
                    const double* log_u, int* n_acc, double* la, int u, cudaStream_t st, int c0 = 0,
-                   int c1 = -1, int* counter = nullptr)
+                   int c1 = -1, int* counter = nullptr, int lane = 0)
 {
     if (c1 < 0) c1 = P->n_chains;
     const int eb0 = P->h_E_slots[c0].begin, eb1 = P->h_E_slots[c1 - 1].end;
@@ -643,7 +671,7 @@ int run_one_update(const pamd_problem* p, Plan* P, R* pos, R* grad, double* S, c
     R* gprop = reinterpret_cast<R*>(P->d_gprop);
     PAMD_CUDA_TRY(launch_mala_propose<R>(P->d_all + eb0, eb1 - eb0, pos, grad, noise, prop,
                                          P->d_part_qf + eb0, P->d_md, u, st));
-    int rc = run_action<R>(p, P, prop, gprop, P->d_Sprop, true, st, c0, c1, counter);
+    int rc = run_action<R>(p, P, prop, gprop, P->d_Sprop, true, st, c0, c1, counter, lane);
     if (rc) return rc;
     PAMD_CUDA_TRY(launch_mala_reverse<R>(P->d_all + eb0, eb1 - eb0, pos, prop, gprop,
                                          P->d_part_qr + eb0, P->d_md, st));
@@ -738,7 +766,7 @@ int path_update_pipelined(const pamd_problem* prob, Plan* P, void* pos, void* gr
         PAMD_CUDA_TRY(cudaStreamWaitEvent(cs, P->events[2 * k], 0));
         for (int u = 0; u < n_updates; ++u)
             if ((rc = run_one_update<R>(prob, P, (R*)dpos, (R*)dgrad, dS, nullptr, nullptr, dnacc, dla,
-                                        u, cs, c0, c1, P->d_chunk_counters + k)))
+                                        u, cs, c0, c1, P->d_chunk_counters + k, k & 1)))
                 return rc;
         PAMD_CUDA_TRY(cudaEventRecord(P->events[2 * k + 1], cs));
         PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_out, P->events[2 * k + 1], 0));

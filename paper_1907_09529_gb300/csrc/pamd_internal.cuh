@@ -238,6 +238,7 @@ struct LJSysDev {
     int tpp, lg_tpp;      // threads per particle (power of two) and its log2
     int cap;              // neighbour-list capacity per thread
     int window;           // steps per neighbour-list window (paired kernel)
+    int outer_cap;        // outer-list capacity per thread (paired kernel, global memory)
     LJK<R> k;
 };
 
@@ -265,9 +266,11 @@ cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_ta
 // slot, 512 or 1024 slots) and cap_lane list entries per thread, two to a word.
 size_t lj_paired_smem_bytes(int NT, int cap_lane);
 int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad);
+// outer: per-CTA outer lists, outer_words 32-bit words for each of grid CTAs.
 cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
                              const float* pos, float* grad, double* partials, int* counter, int NT,
-                             size_t smem, int grid, bool with_grad, cudaStream_t st);
+                             size_t smem, int grid, bool with_grad, uint32_t* outer,
+                             long long outer_words, cudaStream_t st);
 
 cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, int T, int n_chains,
                                   long long sys_offset, double L, double rc, cudaStream_t st);
