@@ -486,7 +486,19 @@ def main():
         hacc = torch.zeros(prob.n_chains, dtype=torch.int32).pin_memory()
         pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=5, n_accepted=hacc)
         ne = max(3, min(args.steps, 10))
+        # pinned copy rates of this host link, measured on the same buffers (they vary
+        # between machines and bound the end-to-end time)
+        ce0, ce1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ce0.record(stream)
+        pos.copy_(hpos, non_blocking=True)
+        ce1.record(stream)
         torch.cuda.synchronize()
+        h2d_gbs = hpos.numel() * hpos.element_size() / (ce0.elapsed_time(ce1) * 1e-3) / 1e9
+        ce0.record(stream)
+        hpos.copy_(pos, non_blocking=True)
+        ce1.record(stream)
+        torch.cuda.synchronize()
+        d2h_gbs = hpos.numel() * hpos.element_size() / (ce0.elapsed_time(ce1) * 1e-3) / 1e9
         e2e_clocks = ClockSampler(local)
         e2e_clocks.start()
         t0 = time.perf_counter()
@@ -498,7 +510,8 @@ def main():
         e2e = {"value": units_rank * world / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
                "d2h_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
-               "ms_per_step": t_e2e * 1e3, "sm_mhz": e2e_clk.get("sm_mhz")}
+               "ms_per_step": t_e2e * 1e3, "sm_mhz": e2e_clk.get("sm_mhz"),
+               "pinned_copy_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)}}
 
     # Dominant kernel: the action + adjoint kernel alone (one launch per LJ system
     # + a tiny finalize), timed with events on its stream over the same data.
