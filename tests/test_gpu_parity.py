@@ -141,6 +141,43 @@ def test_results_independent_of_tiling(pamd, name):
         assert torch.equal(g, outs[0][1])
 
 
+def test_lj_far_from_brownian_paths_use_the_fallbacks(pamd):
+    """Slices that jump by ~0.3 sigma (a jittered FCC lattice at every step) make
+    the item-wide outer lists and the window lists overflow the capacities the
+    plan sizes for Brownian steps: particles then build their window lists from
+    every candidate and evaluate every candidate.  S and the gradient must still
+    match the oracle, and be bitwise independent of tile and window."""
+    N, T, B, rho = 256, 40, 2, 0.5
+    L = (N / rho) ** (1.0 / 3.0)
+    x0 = inputs.fcc_lattice(N, L)
+    rng = inputs.rng(77)
+    paths = (x0[None, None] + 0.12 * rng.standard_normal((B, T + 1, 3, N)))
+    paths = paths.astype(np.float32).astype(np.float64)
+    D, beta, dt = 1.0, 1.0, 1e-4
+    system = pamd.System("lj", N, 3, T, B, box=L, rc=2.5)
+    prob = pamd.Problem([system], D, beta, dt)
+    pot = oracle.lennard_jones(L, 2.5)
+    outs = []
+    try:
+        for tile, window in [(16, 0), (40, 2), (7, 24)]:
+            pamd.tune(tile, 0, 0, -1.0, window)
+            buf = _upload(pamd, prob, [paths])
+            S, g = pamd.action_grad(prob, buf)
+            torch.cuda.synchronize()
+            outs.append((S.cpu(), g.cpu()))
+    finally:
+        pamd.tune()
+    for S, g in outs[1:]:
+        assert torch.equal(S, outs[0][0]) and torch.equal(g, outs[0][1])
+    S, g = outs[0]
+    for b in range(B):
+        So, go = oracle.action_grad(pot, paths[b], D, beta, dt)
+        gb = prob.view(g, 0)[b].double().numpy()
+        assert abs(S[b].item() - So) <= 1e-5 * abs(So)
+        assert rel(gb, go) <= 1e-5
+        assert np.abs(gb - go).max() <= 1e-5 * np.abs(go).max()
+
+
 def test_pair_counts_bit_exact(pamd):
     w = inputs.workload("lj500", "small")
     paths = start_paths(w, "fp32")
