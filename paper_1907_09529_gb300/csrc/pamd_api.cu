@@ -435,6 +435,40 @@ int build_plan(const pamd_problem* p, Plan** out)
                 si.tune = choose_lj_tune(p->systems[q], NT, cap_lane_max, P->lj_paired,
                                          std::sqrt(2.0 * p->D * p->dt));
                 cap_used = std::max(cap_used, si.tune.maxnb);
+            }
+            P->lj_NT = NT;
+            P->lj_nmax = nmax;
+            P->lj_smem = P->lj_paired ? lj_paired_smem_bytes(NT, cap_used)
+                                      : lj_smem_bytes(nmax, NT, cap_used, P->fp64);
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int bg = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, true)
+                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, true)
+                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, true);
+            const int bn = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, false)
+                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, false)
+                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, false);
+            if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
+            // One LJ system of equal items: pick the tile near the chosen one whose item
+            // count fills whole rounds of the persistent grid (no part-empty last round),
+            // keeping at least 16 steps per item.
+            if (nlj == 1 && !one) {
+                for (auto& si : P->sys) {
+                    if (si.kind != PAMD_LJ) continue;
+                    const long long G = (long long)bg * sms;
+                    const long long items0 = (long long)si.chains * ((si.T + si.tune.tile_steps - 1) / si.tune.tile_steps);
+                    const long long rounds = (items0 + G - 1) / G;
+                    const long long per_chain = (rounds * G) / si.chains;
+                    if (per_chain >= 1) {
+                        const int tile = (int)((si.T + per_chain - 1) / per_chain);
+                        if (tile >= std::min(16, si.tune.tile_steps)) si.tune.tile_steps = tile;
+                    }
+                }
+            }
+            for (int q = 0; q < (int)P->sys.size(); ++q) {
+                SysInfo& si = P->sys[q];
+                if (si.kind != PAMD_LJ) continue;
                 si.n_tiles = (si.T + si.tune.tile_steps - 1) / si.tune.tile_steps;
                 si.slot0 = slot;
                 for (int b = 0; b < si.chains; ++b) {
@@ -476,20 +510,6 @@ int build_plan(const pamd_problem* p, Plan** out)
                 for (int q : ord) sorted.push_back(items[q]);
                 items.swap(sorted);
             }
-            P->lj_NT = NT;
-            P->lj_nmax = nmax;
-            P->lj_smem = P->lj_paired ? lj_paired_smem_bytes(NT, cap_used)
-                                      : lj_smem_bytes(nmax, NT, cap_used, P->fp64);
-            int dev = 0, sms = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int bg = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, true)
-                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, true)
-                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, true);
-            const int bn = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, false)
-                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, false)
-                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, false);
-            if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
             P->lj_grid_grad = std::max(1, std::min((int)items.size(), bg * sms));
             P->lj_grid_nograd = std::max(1, std::min((int)items.size(), bn * sms));
             if (P->lj_paired) {
