@@ -488,17 +488,20 @@ def main():
         ne = max(3, min(args.steps, 10))
         # pinned copy rates of this host link, measured on the same buffers (they vary
         # between machines and bound the end-to-end time)
+        scratch = torch.empty_like(pos)
+        hscratch = torch.empty_like(hpos).pin_memory()
         ce0, ce1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ce0.record(stream)
-        pos.copy_(hpos, non_blocking=True)
+        scratch.copy_(hpos, non_blocking=True)
         ce1.record(stream)
         torch.cuda.synchronize()
         h2d_gbs = hpos.numel() * hpos.element_size() / (ce0.elapsed_time(ce1) * 1e-3) / 1e9
         ce0.record(stream)
-        hpos.copy_(pos, non_blocking=True)
+        hscratch.copy_(scratch, non_blocking=True)
         ce1.record(stream)
         torch.cuda.synchronize()
         d2h_gbs = hpos.numel() * hpos.element_size() / (ce0.elapsed_time(ce1) * 1e-3) / 1e9
+        del scratch, hscratch
         e2e_clocks = ClockSampler(local)
         e2e_clocks.start()
         t0 = time.perf_counter()
@@ -512,6 +515,24 @@ def main():
                "d2h_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
                "ms_per_step": t_e2e * 1e3, "sm_mhz": e2e_clk.get("sm_mhz"),
                "pinned_copy_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)}}
+
+    # The ragged workload's full path-sampling loop: 100 updates in one call, which
+    # the library captures once into a CUDA graph and then replays.
+    graph_loop = None
+    if w.name == "ragged" and rank == 0:
+        nup = 100
+        pamd.action_grad(prob, pos, S, grad)  # the cached action and gradient of pos
+        pamd.path_update(prob, pos, grad, S, h, nup, seed=seed, counter=50000, n_accepted=nacc)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        pamd.path_update(prob, pos, grad, S, h, nup, seed=seed, counter=60000, n_accepted=nacc)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1)
+        graph_loop = {"updates_per_call": nup, "ms_per_call": gms, "ms_per_update": gms / nup,
+                      "value": units_rank * nup / (gms * 1e-3), "unit": UNIT,
+                      "note": "one pamd_path_update call of 100 updates, replayed from its captured CUDA graph"}
 
     # Dominant kernel: the action + adjoint kernel alone (one launch per LJ system
     # + a tiny finalize), timed with events on its stream over the same data.
@@ -601,7 +622,7 @@ def main():
                        "lj_launch_shape": tuned or "default"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plain_fp64": plain,
             "gpu_launches": args.steps * (launches_per_update(prob)) + 1 * args.steps,
-            "clocks": clk, "accept_rate": float(nacc.sum().item()) / max(
+            "clocks": clk, "graph_loop": graph_loop, "accept_rate": float(nacc.sum().item()) / max(
                 1, prob.n_chains * (args.steps + args.warmup)),
         }
         print(json.dumps(out), flush=True)
