@@ -40,10 +40,10 @@
 // slice), which holds every pair that any of the item's windows can need; it
 // sits in global memory (one region per CTA, L2-resident).  A particle whose
 // outer list overflows builds its window lists from all candidates; one whose
-// window list overflows scans all candidates.  Candidates are visited in increasing j in every case, so each
-// force and Hessian sum runs over the in-cutoff pairs in one fixed order
-// whatever the tiling, window or list capacity, and the results are bitwise
-// independent of them.
+// window list overflows scans all candidates.  Candidates are visited in
+// increasing j in every case, so each force and Hessian sum runs over the
+// in-cutoff pairs in one fixed order whatever the tiling, window or list
+// capacity, and the results are bitwise independent of them.
 #include "pamd_internal.cuh"
 
 namespace pamd {
