@@ -583,9 +583,12 @@ def main():
                 "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
                 "bytes_per_launch": nbytes, "kernel_ms": ms_kernel}
 
-    # Plain single-path FP64 form of the same action + gradient (one chain per launch).
+    # Plain single-path FP64 form of the same action + gradient (one chain per launch),
+    # with the library's automatic launch shape (not the shape tuned for the batched
+    # single-precision kernel above).
     plain = None
     if not args.no_plain and rank == 0:
+        pamd.tune()
         p64 = pamd.Problem(systems, w.D, w.beta, w.dt, "fp64", one_chain_per_launch=True)
         pos64 = pos.double()
         S64, g64 = pamd.action_grad(p64, pos64)
