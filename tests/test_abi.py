@@ -62,3 +62,21 @@ def test_problem_layout_host_logic():
     assert p.units == 108 * 10 * 2 + 17 * 3
     buf = p.empty("cpu")
     assert p.view(buf, 1).shape == (3, 18, 3, 1)
+
+
+def test_tune_accepts_the_autotuner_shapes_and_rejects_bad_ones():
+    """pamd_tune is host-only (no CUDA call): every autotuner shape is accepted,
+    sizes that cannot work are refused with PAMD_ERR_ARG."""
+    import paper_1907_09529_gb300 as pamd
+    from paper_1907_09529_gb300 import _lib, autotune
+    try:
+        shapes = list(autotune.candidates(tiles=(32, 192), windows=(2, 12)))
+        assert shapes and all(len(s) == 5 for s in shapes)
+        for shape in shapes:
+            pamd.tune(*shape)
+        lib = _lib.load()
+        for bad in [(-1, 0, 0, -1.0, 0), (0, 3, 0, -1.0, 0), (0, 0, -5, -1.0, 0),
+                    (0, 0, 0, -1.0, 1), (0, 0, 0, -1.0, -2)]:
+            assert lib.pamd_tune(*bad) == _lib.PAMD_ERR_ARG, bad
+    finally:
+        pamd.tune()
