@@ -87,6 +87,33 @@ struct Smem {
     __device__ float2& z(int o8) const { return *reinterpret_cast<float2*>(base + 32 * NMAX + o8); }
     __device__ float2& rz(int o8) const { return *reinterpret_cast<float2*>(base + 40 * NMAX + o8); }
     __device__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 48 * NMAX); }
+    // staging area of list references {x, y, z, delta}: the residual array
+    __device__ float4& ref(int o8) const { return rxy(o8); }
+};
+
+// Layout of the pipelined form (see paired_item_pipe): two position buffers, the
+// residuals and a separate staging area (the residuals stay live across list builds).
+//   [0, 32 NMAX)        xy of buffers 0 and 1
+//   [32 NMAX, 48 NMAX)  rxy
+//   [48 NMAX, 64 NMAX)  staged references {x, y, z, delta}
+//   [64 NMAX, 80 NMAX)  z of buffers 0 and 1
+//   [80 NMAX, 88 NMAX)  rz
+//   [88 NMAX, ...)      neighbour lists
+template <int NMAX>
+struct SmemP {
+    unsigned char* base;
+    __device__ float4& xy(int buf, int o8) const
+    {
+        return *reinterpret_cast<float4*>(base + 16 * NMAX * buf + 2 * o8);
+    }
+    __device__ float2& z(int buf, int o8) const
+    {
+        return *reinterpret_cast<float2*>(base + 64 * NMAX + 8 * NMAX * buf + o8);
+    }
+    __device__ float4& rxy(int o8) const { return *reinterpret_cast<float4*>(base + 32 * NMAX + 2 * o8); }
+    __device__ float2& rz(int o8) const { return *reinterpret_cast<float2*>(base + 80 * NMAX + o8); }
+    __device__ float4& ref(int o8) const { return *reinterpret_cast<float4*>(base + 48 * NMAX + 2 * o8); }
+    __device__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 88 * NMAX); }
 };
 
 // Packed constants of one system (built per item from the per-system table).
@@ -178,10 +205,11 @@ struct PairList {
 
     // Pair test at the staged reference {x, y, z, delta} (residual array) of
     // two candidates: r_ij(x_c) <= rc + delta_i + delta_j for each half.
-    __device__ __forceinline__ void test2(const Smem<NMAX>& P, const K2& k, float4 pi, int o1,
-                                          int o2, bool& in1, bool& in2) const
+    template <class SM>
+    __device__ __forceinline__ void test2(const SM& P, const K2& k, float4 pi, int o1, int o2,
+                                          bool& in1, bool& in2) const
     {
-        const float4 A = P.rxy(o1), B = P.rxy(o2);
+        const float4 A = P.ref(o1), B = P.ref(o2);
         float2 dx = sub2(pk(pi.x), pk(A.x, B.x));
         float2 dy = sub2(pk(pi.y), pk(A.y, B.y));
         float2 dz = sub2(pk(pi.z), pk(A.z, B.z));
@@ -197,12 +225,13 @@ struct PairList {
 
     // Outer list of the item (reference and item-wide margins staged): all
     // candidates j = q (mod tpp), in increasing j.
-    __device__ void build_outer(const Smem<NMAX>& P, const K2& k)
+    template <class SM>
+    __device__ void build_outer(const SM& P, const K2& k)
     {
         ocnt = 0;
         oovf = true;
         if (!active) return;
-        const float4 pi = P.rxy(8 * i);
+        const float4 pi = P.ref(8 * i);
         int c = 0;
         auto add = [&](bool in, int o8) {
             if (in) {
@@ -225,12 +254,13 @@ struct PairList {
 
     // Window list (window reference and margins staged) from the outer list,
     // or from all candidates if the outer list overflowed; increasing j.
-    __device__ void build(const Smem<NMAX>& P, const K2& k)
+    template <class SM>
+    __device__ void build(const SM& P, const K2& k)
     {
         cnt = 0;
         ovf = false;
         if (!active) return;
-        const float4 pi = P.rxy(8 * i);
+        const float4 pi = P.ref(8 * i);
         int c = 0;
         auto add = [&](bool in, int o8) {
             if (in) {
@@ -338,6 +368,51 @@ struct PairList {
         }
         group_sum(hx, hy, hz);
     }
+
+    // One walk over the list for the pipelined form: the Hessian-vector product of
+    // the pair in buffer hb with the residual array (DO_H) and the force of the
+    // pair in buffer fb (DO_F).  Each result equals that of hvp() / force() on
+    // the same slices: the two chains of arithmetic are only interleaved.
+    template <bool DO_H, bool DO_F>
+    __device__ void combined(const SmemP<NMAX>& P, int hb, int fb, float2 vix, float2 viy,
+                             float2 viz, const K2& k, float2& hx, float2& hy, float2& hz,
+                             float2& fx, float2& fy, float2& fz) const
+    {
+        hx = hy = hz = fx = fy = fz = pk(0.0f);
+        if (active) {
+            const float4 hxy = P.xy(hb, 8 * i);
+            const float2 hxi = pk(hxy.x, hxy.y), hyi = pk(hxy.z, hxy.w), hzi = P.z(hb, 8 * i);
+            const float4 fxy = P.xy(fb, 8 * i);
+            const float2 fxi = pk(fxy.x, fxy.y), fyi = pk(fxy.z, fxy.w), fzi = P.z(fb, 8 * i);
+            for_each_candidate([&](int o8) {
+                if (DO_H) {
+                    float2 dx, dy, dz, w, ir2, ir6;
+                    const float2 r2 = pair_geom(hxi, hyi, hzi, P.xy(hb, o8), P.z(hb, o8), k, dx, dy, dz);
+                    const float2 fs = pair_fs(r2, k, w, ir2, ir6);
+                    const float2 Bc = mul2(fma2(w, fma2(k.c3, ir6, k.m7), fs), ir2);
+                    const float2 nfs = mul2(fs, k.m1);
+                    const float4 vj = P.rxy(o8);
+                    const float2 vx = sub2(vix, pk(vj.x, vj.y));
+                    const float2 vy = sub2(viy, pk(vj.z, vj.w));
+                    const float2 vz = sub2(viz, P.rz(o8));
+                    const float2 bd = mul2(Bc, fma2(dz, vz, fma2(dy, vy, mul2(dx, vx))));
+                    hx = fma2(nfs, vx, fma2(bd, dx, hx));
+                    hy = fma2(nfs, vy, fma2(bd, dy, hy));
+                    hz = fma2(nfs, vz, fma2(bd, dz, hz));
+                }
+                if (DO_F) {
+                    float2 dx, dy, dz, w, ir2, ir6;
+                    const float2 r2 = pair_geom(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz);
+                    const float2 fs = pair_fs(r2, k, w, ir2, ir6);
+                    fx = fma2(fs, dx, fx);
+                    fy = fma2(fs, dy, fy);
+                    fz = fma2(fs, dz, fz);
+                }
+            });
+        }
+        if (DO_H) group_sum(hx, hy, hz);
+        if (DO_F) group_sum(fx, fy, fz);
+    }
 };
 
 __device__ __forceinline__ float sq3(float x, float y, float z)
@@ -405,7 +480,7 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
             }
             // delta rounded up: sqrt and the sums above are within a few ulp
             const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
-            P.rxy(8 * n) = make_float4(cx, cy, cz, delta);
+            P.ref(8 * n) = make_float4(cx, cy, cz, delta);
         }
     };
 
@@ -507,9 +582,199 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
     if (threadIdx.x == 0) partials[I.slot] = tot;
 }
 
+// One work item, action and gradient, pipelined over step pairs: the list walk of
+// pair p computes the Hessian-vector product of pair p and the force of pair p+1
+// (two independent chains of arithmetic per list entry, one index load), so the
+// positions of two pairs are resident.  Window lists cover two consecutive pairs;
+// windows are at least 4 steps long and overlap by one pair.  Every sum is the
+// same as in paired_item.
+template <int NMAX>
+__device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev<float>& S,
+                                                 unsigned char* smem, const float* __restrict__ pos,
+                                                 float* __restrict__ grad,
+                                                 double* __restrict__ partials, double* red,
+                                                 uint32_t* outer)
+{
+    const int N = S.N;
+    const SmemP<NMAX> P{smem};
+    PairList<NMAX> L;
+    L.init(N, S.tpp, S.lg_tpp, S.cap, P.list(), S.outer_cap, outer);
+    const K2 k(S.k);
+    const float2 na = pk(-k.a), ginv = pk(k.ginv);
+
+    const int t0 = I.t0, t1 = I.t1, T = S.T;
+    const int s = 3 * N;
+    const float* __restrict__ X = pos + S.off + (long long)I.chain * S.chain_len;
+    float* __restrict__ G = grad + S.off + (long long)I.chain * S.chain_len;
+    const int i = L.i;
+    const bool lead = L.active && L.q == 0;
+    const int ts = t0 > 0 ? t0 - 1 : t0;  // first slice of the first pair
+
+    auto fetch = [&](int a, int n, float (&v)[6]) {
+        const float* A = X + (long long)a * s + n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[2 * c] = __ldg(A + c * N);
+            v[2 * c + 1] = __ldg(A + s + c * N);
+        }
+    };
+    auto store = [&](int buf, int n, const float (&v)[6]) {
+        P.xy(buf, 8 * n) = make_float4(v[0], v[1], v[2], v[3]);
+        P.z(buf, 8 * n) = make_float2(v[4], v[5]);
+    };
+    auto stage = [&](int lo, int hi) {
+        const int c = lo + (hi - 1 - lo) / 2;
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            const float* A = X + n;
+            const float* C = A + (long long)c * s;
+            const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
+            float d2 = 0.0f;
+#pragma unroll 4
+            for (int t = lo; t < hi; ++t) {
+                const float* Q = A + (long long)t * s;
+                const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
+                d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
+            }
+            const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
+            P.ref(8 * n) = make_float4(cx, cy, cz, delta);
+        }
+    };
+    const int W = max(4, S.window);
+    int win_end = ts;
+    // Window list covering slices up to `last` (the b slice of the later of the two
+    // pairs the next walk touches), starting at slice a.
+    auto ensure_window = [&](int a, int last) {
+        if (last < win_end) return;
+        const int e = min(a + W, t1 + 1);  // > last: last <= a + 3 <= a + W, or last <= t1
+        stage(a, e);
+        __syncthreads();
+        L.build(P, k);
+        __syncthreads();
+        win_end = e;
+    };
+    // residuals of the pair starting at slice a (in buffer buf), F its force
+    auto residual = [&](int buf, int a, float2 fx, float2 fy, float2 fz, float2& rx, float2& ry,
+                        float2& rz) {
+        rx = ry = rz = pk(0.0f);
+        if (!L.active) return;
+        const int b = a + 1;
+        const bool hb = b < t1;
+        float xn = 0.0f, yn = 0.0f, zn = 0.0f;
+        if (hb) {
+            const float* Xb1 = X + (long long)(b + 1) * s + i;
+            xn = __ldg(Xb1);
+            yn = __ldg(Xb1 + N);
+            zn = __ldg(Xb1 + 2 * N);
+        }
+        const float4 pxy = P.xy(buf, 8 * i);
+        const float2 pz = P.z(buf, 8 * i);
+        rx = fma2(na, fx, sub2(pk(pxy.y, xn), pk(pxy.x, pxy.y)));
+        ry = fma2(na, fy, sub2(pk(pxy.w, yn), pk(pxy.z, pxy.w)));
+        rz = fma2(na, fz, sub2(pk(pz.y, zn), pz));
+        if (!hb) rx.y = ry.y = rz.y = 0.0f;
+    };
+    double acc = 0.0;
+    auto account = [&](int a, float2 rx, float2 ry, float2 rz) {
+        if (!lead) return;
+        P.rxy(8 * i) = make_float4(rx.x, rx.y, ry.x, ry.y);
+        P.rz(8 * i) = rz;
+        if (a >= t0) acc += (double)sq3(rx.x, ry.x, rz.x);
+        if (a + 1 < t1) acc += (double)sq3(rx.y, ry.y, rz.y);
+    };
+
+    // Item-wide outer list.
+    stage(ts, t1 + 1);
+    __syncthreads();
+    L.build_outer(P, k);
+    __syncthreads();
+
+    // Pairs a = ts + 2p, p < np; buffers: pair p in buffer p & 1.
+    const int np = (t1 - ts + 1) / 2;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        float v[6];
+        fetch(ts, n, v);
+        store(0, n, v);
+        if (np > 1) {
+            fetch(ts + 2, n, v);
+            store(1, n, v);
+        }
+    }
+    __syncthreads();
+    ensure_window(ts, min(ts + (np > 1 ? 3 : 1), t1));
+
+    // Prologue: force and residuals of pair 0.
+    float2 rx, ry, rz;  // residuals of the current pair
+    {
+        float2 hx, hy, hz, fx, fy, fz;
+        L.template combined<false, true>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx, hy, hz, fx,
+                                         fy, fz);
+        residual(0, ts, fx, fy, fz, rx, ry, rz);
+        account(ts, rx, ry, rz);
+    }
+    __syncthreads();
+
+    float rpx = 0.0f, rpy = 0.0f, rpz = 0.0f;  // r_{a-1}
+    for (int p = 0; p < np; ++p) {
+        const int cur = p & 1, nxt = cur ^ 1;
+        const int a = ts + 2 * p, b = a + 1;
+        const bool hasb = b < t1, real_a = a >= t0;
+        const bool next = p + 1 < np;
+        // prefetch pair p+2 (its slices a+4, a+5 <= t1 when it exists)
+        const bool pf = p + 2 < np && (int)threadIdx.x < N;
+        float nv[6];
+        if (pf) fetch(a + 4, threadIdx.x, nv);
+
+        float2 hx, hy, hz, fx, fy, fz;
+        if (next)
+            L.template combined<true, true>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+        else
+            L.template combined<true, false>(P, cur, cur, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+        if (lead) {
+            const float2 gx = mul2(fma2(pk(k.a), hx, sub2(pk(rpx, rx.x), rx)), ginv);
+            const float2 gy = mul2(fma2(pk(k.a), hy, sub2(pk(rpy, ry.x), ry)), ginv);
+            const float2 gz = mul2(fma2(pk(k.a), hz, sub2(pk(rpz, rz.x), rz)), ginv);
+            if (real_a) {
+                float* Ga = G + (long long)a * s + i;
+                Ga[0] = gx.x;
+                Ga[N] = gy.x;
+                Ga[2 * N] = gz.x;
+            }
+            if (hasb) {
+                float* Gb = G + (long long)b * s + i;
+                Gb[0] = gx.y;
+                Gb[N] = gy.y;
+                Gb[2 * N] = gz.y;
+            }
+        }
+        rpx = hasb ? rx.y : rx.x;
+        rpy = hasb ? ry.y : ry.x;
+        rpz = hasb ? rz.y : rz.x;
+        float2 nrx, nry, nrz;
+        if (next) residual(nxt, a + 2, fx, fy, fz, nrx, nry, nrz);
+        __syncthreads();  // every walk is done with the residuals and buffer cur
+        if (next) {
+            account(a + 2, nrx, nry, nrz);
+            rx = nrx;
+            ry = nry;
+            rz = nrz;
+        }
+        if (pf) store(cur, threadIdx.x, nv);
+        if (next) ensure_window(a + 2, min(a + (p + 2 < np ? 5 : 3), t1));
+        __syncthreads();
+    }
+    if (t1 == T && lead) {
+        float* Gt = G + (long long)T * s + i;
+        Gt[0] = rpx * k.ginv;
+        Gt[N] = rpy * k.ginv;
+        Gt[2 * N] = rpz * k.ginv;
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[I.slot] = tot;
+}
+
 // Persistent grid: each CTA takes items from *counter until none is left.
 // Systems must have N <= MAXT (the block size is at most MAXT).
-template <bool GRAD, int MAXT>
+template <bool GRAD, int MAXT, bool PIPE>
 __global__ void __launch_bounds__(MAXT, 1)
     lj_paired_kernel(const LJItem* __restrict__ items, int n_items,
                      const LJSysDev<float>* __restrict__ systems, const float* __restrict__ pos,
@@ -527,28 +792,36 @@ __global__ void __launch_bounds__(MAXT, 1)
         if (it >= n_items) break;
         const LJItem I = items[it];
         const LJSysDev<float> S = systems[I.sys];
-        paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red,
-                                outer + (long long)blockIdx.x * outer_words);
+        if (GRAD && PIPE)
+            paired_item_pipe<MAXT>(I, S, smem_raw, pos, grad, partials, red,
+                                   outer + (long long)blockIdx.x * outer_words);
+        else
+            paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red,
+                                    outer + (long long)blockIdx.x * outer_words);
     }
 }
 
+// The pipelined form is used with the gradient for blocks of up to 512 threads
+// (its two position buffers and staging area take 88 bytes per particle slot).
 template <bool GRAD>
-auto paired_kernel_ptr(int NT)
+auto paired_kernel_ptr(int NT, bool pipe)
 {
-    return NT <= 512 ? lj_paired_kernel<GRAD, 512> : lj_paired_kernel<GRAD, 1024>;
+    if (GRAD && pipe && NT <= 512) return lj_paired_kernel<GRAD, 512, true>;
+    return NT <= 512 ? lj_paired_kernel<GRAD, 512, false> : lj_paired_kernel<GRAD, 1024, false>;
 }
 
 }  // namespace
 
-size_t lj_paired_smem_bytes(int NT, int cap_lane)
+size_t lj_paired_smem_bytes(int NT, int cap_lane, bool pipe)
 {
     const size_t nmax = NT <= 512 ? 512 : 1024;
-    return 48 * nmax + (size_t)(cap_lane / 2) * NT * sizeof(uint32_t);
+    const size_t slots = (pipe && NT <= 512) ? 88 : 48;
+    return slots * nmax + (size_t)(cap_lane / 2) * NT * sizeof(uint32_t);
 }
 
-int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad)
+int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad, bool pipe)
 {
-    auto kern = with_grad ? paired_kernel_ptr<true>(NT) : paired_kernel_ptr<false>(NT);
+    auto kern = with_grad ? paired_kernel_ptr<true>(NT, pipe) : paired_kernel_ptr<false>(NT, pipe);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
@@ -559,14 +832,14 @@ int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad)
 
 cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
                              const float* pos, float* grad, double* partials, int* counter, int NT,
-                             size_t smem, int grid, bool with_grad, uint32_t* outer,
+                             size_t smem, int grid, bool with_grad, bool pipe, uint32_t* outer,
                              long long outer_words, cudaStream_t st)
 {
     if (n_items <= 0) return cudaSuccess;
     if (NT > 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    auto kern = with_grad ? paired_kernel_ptr<true>(NT) : paired_kernel_ptr<false>(NT);
+    auto kern = with_grad ? paired_kernel_ptr<true>(NT, pipe) : paired_kernel_ptr<false>(NT, pipe);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, smem, st>>>(items, n_items, static_cast<const LJSysDev<float>*>(sys_table),

@@ -89,6 +89,7 @@ struct Plan {
     // LJ work items (persistent kernel)
     int lj_NT = 0, lj_nmax = 0, lj_grid_grad = 0, lj_grid_nograd = 0;
     bool lj_paired = false;  // single precision: two steps per thread (lj_paired.cu)
+    bool lj_pipe = false;    // ... with the gradient pass pipelined over step pairs
     size_t lj_smem = 0;
     std::vector<unsigned char> h_lj_sys;  // host copy of the system table
     size_t lj_sys_stride = 0;
@@ -419,7 +420,9 @@ int build_plan(const pamd_problem* p, Plan** out)
             // Single precision runs the paired-step kernel, one CTA per SM: its list
             // may use all the shared memory beside two packed slices of 32 bytes.
             P->lj_paired = !P->fp64 && std::getenv("PAMD_LJ_ONE_STEP") == nullptr;
-            const long long slices = P->lj_paired ? 48LL * (NT <= 512 ? 512 : 1024) : 3 * (long long)nmax * v4;
+            P->lj_pipe = P->lj_paired && NT <= 512 && std::getenv("PAMD_LJ_NO_PIPE") == nullptr;
+            const long long slices = P->lj_paired ? (P->lj_pipe ? 88LL * 512 : 48LL * (NT <= 512 ? 512 : 1024))
+                                                  : 3 * (long long)nmax * v4;
             const int budget = (NT <= 512 && !P->fp64 && !P->lj_paired && g_tune_override.maxnb <= 0)
                                    ? 113 * 1024
                                    : max_dynamic_smem() - 1024;
@@ -438,15 +441,15 @@ int build_plan(const pamd_problem* p, Plan** out)
             }
             P->lj_NT = NT;
             P->lj_nmax = nmax;
-            P->lj_smem = P->lj_paired ? lj_paired_smem_bytes(NT, cap_used)
+            P->lj_smem = P->lj_paired ? lj_paired_smem_bytes(NT, cap_used, P->lj_pipe)
                                       : lj_smem_bytes(nmax, NT, cap_used, P->fp64);
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int bg = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, true)
+            const int bg = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, true, P->lj_pipe)
                            : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, true)
                                         : lj_blocks_per_sm<float>(NT, P->lj_smem, true);
-            const int bn = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, false)
+            const int bn = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, false, P->lj_pipe)
                            : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, false)
                                         : lj_blocks_per_sm<float>(NT, P->lj_smem, false);
             if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
@@ -652,7 +655,7 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
             if (std::is_same<R, float>::value && P->lj_paired)
                 return launch_lj_paired(
                     items, n, P->d_lj_sys, (const float*)pos, (float*)grad, P->d_part_S, counter,
-                    P->lj_NT, P->lj_smem, g, with_grad,
+                    P->lj_NT, P->lj_smem, g, with_grad, P->lj_pipe,
                     P->d_outer + (long long)lane * std::max(P->lj_grid_grad, P->lj_grid_nograd) *
                                      P->outer_words,
                     P->outer_words, st);

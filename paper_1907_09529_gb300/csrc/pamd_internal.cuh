@@ -264,12 +264,13 @@ cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_ta
 // packed f32x2 pair arithmetic (lj_paired.cu), for systems of N <= NT <= 1024.
 // Shared memory: positions and residuals of two slices (48 bytes per particle
 // slot, 512 or 1024 slots) and cap_lane list entries per thread, two to a word.
-size_t lj_paired_smem_bytes(int NT, int cap_lane);
-int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad);
+// pipe: the gradient launch uses the pipelined form (blocks of <= 512 threads).
+size_t lj_paired_smem_bytes(int NT, int cap_lane, bool pipe);
+int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad, bool pipe);
 // outer: per-CTA outer lists, outer_words 32-bit words for each of grid CTAs.
 cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
                              const float* pos, float* grad, double* partials, int* counter, int NT,
-                             size_t smem, int grid, bool with_grad, uint32_t* outer,
+                             size_t smem, int grid, bool with_grad, bool pipe, uint32_t* outer,
                              long long outer_words, cudaStream_t st);
 
 cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, int T, int n_chains,
