@@ -417,8 +417,9 @@ int build_plan(const pamd_problem* p, Plan** out)
         if (nlj) {
             const int NT = choose_lj_block(p);
             const size_t v4 = P->fp64 ? 32 : 16;
-            // Single precision runs the paired-step kernel, one CTA per SM: its list
-            // may use all the shared memory beside two packed slices of 32 bytes.
+            // Single precision runs the paired-step kernel, one CTA per SM: its lists
+            // may use all the shared memory beside the packed slices (48 bytes per
+            // particle slot, 88 in the pipelined gradient form).
             P->lj_paired = !P->fp64 && std::getenv("PAMD_LJ_ONE_STEP") == nullptr;
             P->lj_pipe = P->lj_paired && NT <= 512 && std::getenv("PAMD_LJ_NO_PIPE") == nullptr;
             const long long slices = P->lj_paired ? (P->lj_pipe ? 88LL * 512 : 48LL * (NT <= 512 ? 512 : 1024))
