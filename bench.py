@@ -39,8 +39,6 @@ UNIT = "particle-timeslices/s"
 FLOPS_PER_PAIR = 75
 FLOPS_PER_UNIT = 23
 # Harmonic action + gradient: read x once, write g once per coordinate.
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 
 
 def parse():
@@ -241,6 +239,45 @@ def run_reference(args, w):
 
 
 # ------------------------------------------------------------------ GPU leg
+def measure_fp32_peak(dev, stream, target_ms=60.0):
+    """FP32 FMA throughput of this GPU, measured with the library's probe kernel
+    (8 independent dependent FMA chains per thread, two 1024-thread CTAs per SM;
+    scalar fma.rn.f32 and packed fma.rn.f32x2).  Best of 3 timed launches after a
+    warm-up, CUDA events on the launching stream, SM clocks sampled meanwhile."""
+    import ctypes
+    import torch
+    from paper_1907_09529_gb300 import _lib
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 2 * sms, 1024
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    res = {"sms": sms, "blocks": blocks, "threads": threads}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    for packed in (0, 1):
+        iters = 20000
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # size the launch to about target_ms
+        e0.record(stream)
+        _lib.pamd_fp32_fma_probe(packed, blocks, threads, iters, ctypes.c_void_p(out.data_ptr()), sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        iters = max(1000, int(iters * target_ms / max(e0.elapsed_time(e1), 1e-3)))
+        best = 0.0
+        for _ in range(4):
+            e0.record(stream)
+            fl = _lib.pamd_fp32_fma_probe(packed, blocks, threads, iters,
+                                          ctypes.c_void_p(out.data_ptr()), sp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        res["packed_tflops" if packed else "scalar_tflops"] = best
+    clk = clocks.stop()
+    res["sm_mhz"] = clk.get("sm_mhz")
+    res["peak_tflops"] = max(res["scalar_tflops"], res["packed_tflops"])
+    return res
+
+
 def rank_seed(w, rank: int) -> int:
     """Every rank draws its own chains: the workload is replicated with a
     rank-dependent seed (weak scaling, no data exchanged between ranks)."""
@@ -566,11 +603,17 @@ def main():
             off += nsl
         flops = FLOPS_PER_PAIR * pairs + FLOPS_PER_UNIT * units_rank
         achieved = flops / (ms_kernel * 1e-3) / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        probe = measure_fp32_peak(dev, stream)
+        peak = probe["peak_tflops"]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(args.config, "lj_paired_kernel"),
                 "kernel": "lj_paired_kernel<GRAD=1,512>",
-                "peak_note": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)",
+                "peak_note": ("of measured: FP32 FMA throughput probe in this run "
+                              f"({probe['sms']} SMs, FMA = 2 flops; scalar "
+                              f"{probe['scalar_tflops']:.1f}, packed f32x2 "
+                              f"{probe['packed_tflops']:.1f} TFLOP/s at a median "
+                              f"{probe['sm_mhz']} MHz; peak = the larger)"),
+                "fp32_probe": probe,
                 "pairs_per_launch": pairs, "flops_per_launch": flops, "kernel_ms": ms_kernel}
     else:
         nbytes = sum(s.n_chains * (s.T + 1) * s.d * s.N for s in w.systems) * 4 * 2

@@ -60,7 +60,8 @@ extern "C" {
 #define PAMD_ERR_ARG (-1)          /* invalid argument or shape */
 #define PAMD_ERR_UNSUPPORTED (-2)  /* valid, but outside what the kernels handle */
 #define PAMD_ERR_CUDA (-3)         /* a CUDA runtime call or launch failed */
-#define PAMD_ERR_TIMEOUT (-4)      /* a bounded device wait ran out */
+#define PAMD_ERR_TIMEOUT (-4)      /* a bounded device wait ran out (reserved: no kernel of
+                                      this library waits on another, so no call returns it) */
 #define PAMD_ERR_NONFINITE (-5)    /* a non-finite action was produced */
 #define PAMD_ERR_ALLOC (-6)        /* workspace allocation failed */
 
@@ -304,14 +305,18 @@ int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, doub
  * that array until the process exits.
  *   prob : harmonic systems only (PAMD_FP32 or PAMD_FP64); otherwise
  *          PAMD_ERR_ARG.  A problem needing more than PAMD_NOALLOC_MAX_BLOCKS
- *          blocks (sum over chains of ceil((T+1)*dim*N / 4096)) is rejected
- *          with PAMD_ERR_UNSUPPORTED before anything runs.
- *   pos, S, grad : device pointers (host pointers: PAMD_ERR_ARG), as in
- *          pamd_action_grad.
- * No cudaMalloc, cudaFree or allocating library call is made.  The first call
- * on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ *          blocks (sum over chains of ceil((T+1)*dim*N / 4096)), or with a
+ *          system of more than 65535 chains, is rejected with
+ *          PAMD_ERR_UNSUPPORTED before anything is enqueued.
+ *   pos, S, grad : device pointers on the current device (host pointers, or
+ *          another device's memory: PAMD_ERR_ARG), as in pamd_action_grad.
+ * No cudaMalloc, cudaFree or allocating library call is made.  Every call made
+ * outside stream capture looks up the scratch array's device address
+ * (cudaGetSymbolAddress) on the current device, so the address stays right
+ * after a device reset; a call made while `stream` is capturing uses the
+ * address found by an earlier uncaptured call on that device, so make one
+ * call on each device before any stream capture (otherwise PAMD_ERR_CUDA).
+ * All calls share the one array and it keeps the
  * last call's contents (every block sum is written before it is read, so
  * nothing needs clearing); calls whose kernels overlap on the GPU -- on two
  * streams, or from two threads -- race on it and must be serialised by the
@@ -320,8 +325,28 @@ int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, doub
 int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void* pos, double* S, void* grad,
                                 void* stream);
 
+/* Measured FP32 fused multiply-add throughput, the denominator of the
+ * single-precision roofline (a diagnostic; the paper has no counterpart).
+ * Launches `blocks` CTAs of `threads` threads on `stream`; every thread runs 8
+ * independent chains of `iters` dependent FMAs, scalar (packed == 0) or packed
+ * two-wide f32x2 instructions (packed != 0).  The caller times the launch (CUDA
+ * events on `stream`) and divides *flops (FMA = 2 flops, written on return) by
+ * the duration.
+ *   out   : float[blocks * threads], device memory, written (keeps the chains live).
+ *   flops : host double, written; may be NULL.
+ * PAMD_ERR_ARG for a non-device `out`, threads not a multiple of 32 in
+ * [32, 1024], or blocks / iters < 1. */
+int pamd_fp32_fma_probe(int packed, int blocks, int threads, int iters, float* out,
+                        double* flops, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* pamd_status_string(int status);
+
+/* Numbers of cached plans (one per problem shape and launch-shape override)
+ * and of captured update graphs (one per plan, buffer set and update count):
+ * a loop that repeats a call on the same buffers must leave both unchanged.
+ * Either pointer may be NULL.  Host-side; no device work. */
+int pamd_cache_stats(int* n_plans, int* n_graphs);
 
 /* Free every cached plan, workspace and graph (synchronises the device). */
 int pamd_release_cache(void);

@@ -21,7 +21,7 @@ from ._lib import (PAMD_FLAG_HO_EXACT_PROPAGATOR, PAMD_FLAG_ONE_CHAIN_PER_LAUNCH
                    PamdError, pamd_action, pamd_action_grad, pamd_device_status, pamd_euler_reference,
                    pamd_event, pamd_fragment_mc, pamd_shift_regenerate,
                    pamd_lj_pair_counts, pamd_normals, pamd_path_update, pamd_philox,
-                   pamd_release_cache, pamd_tune, pamd_version)
+                   pamd_cache_stats, pamd_release_cache, pamd_tune, pamd_version)
 
 __all__ = [
     "System", "Problem", "action", "action_grad", "path_update", "euler_reference",
@@ -29,7 +29,7 @@ __all__ = [
     "pamd_action", "pamd_action_grad", "pamd_path_update", "pamd_euler_reference",
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_release_cache", "pamd_tune",
     "pamd_version", "pamd_device_status", "device_status", "pamd_fragment_mc", "fragment_mc",
-    "fragment_slots", "pamd_shift_regenerate", "pamd_event",
+    "fragment_slots", "pamd_shift_regenerate", "pamd_event", "pamd_cache_stats", "cache_stats",
 ]
 
 ALIGN = 8  # system offsets are rounded to 8 elements (>= 16 bytes)
@@ -225,6 +225,11 @@ def tune(tile_steps: int = 0, threads_per_particle: int = 0, max_neighbours: int
 
 def release_cache():
     pamd_release_cache()
+
+
+def cache_stats():
+    """(cached plans, captured update graphs) held by the library."""
+    return pamd_cache_stats()
 
 
 def device_status(stream=None):

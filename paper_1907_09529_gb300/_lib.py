@@ -35,6 +35,7 @@ EXPORTS = (
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
     "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate", "pamd_event",
+    "pamd_cache_stats", "pamd_fp32_fma_probe",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -99,6 +100,9 @@ def load(path: str = LIB_PATH):
                                          ctypes.c_double, ctypes.c_int]),
             "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
             "pamd_device_status": (ctypes.c_int, [_VP]),
+            "pamd_cache_stats": (ctypes.c_int, [_VP, _VP]),
+            "pamd_fp32_fma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, _VP, _VP, _VP]),
             "pamd_fragment_mc": (ctypes.c_int, [_PP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 u64, u64, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
             "pamd_shift_regenerate": (ctypes.c_int, [_PP, _VP, _VP, ctypes.c_int, _VP, u64, u64,
@@ -184,6 +188,21 @@ def pamd_device_status(stream):
 
 def pamd_release_cache():
     return _call("pamd_release_cache")
+
+
+def pamd_cache_stats():
+    """(cached plans, captured update graphs) of the library's cache."""
+    n_plans, n_graphs = ctypes.c_int(0), ctypes.c_int(0)
+    _call("pamd_cache_stats", ctypes.byref(n_plans), ctypes.byref(n_graphs))
+    return n_plans.value, n_graphs.value
+
+
+def pamd_fp32_fma_probe(packed, blocks, threads, iters, out, stream):
+    """Launch the FMA throughput probe; returns the flops it performs."""
+    flops = ctypes.c_double(0.0)
+    _call("pamd_fp32_fma_probe", int(packed), int(blocks), int(threads), int(iters), out,
+          ctypes.byref(flops), stream)
+    return flops.value
 
 
 def pamd_version():

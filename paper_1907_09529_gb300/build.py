@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpamd.so")
 SOURCES = ["pamd_api.cu", "ho_kernels.cu", "lj_kernels.cu", "lj_paired.cu", "update_kernels.cu", "noalloc.cu",
-           "fragment_kernels.cu"]
+           "fragment_kernels.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

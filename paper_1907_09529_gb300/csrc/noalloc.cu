@@ -12,6 +12,7 @@
 // until the process exits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "pamd_internal.cuh"
@@ -25,18 +26,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array for the current device (looked up once
-// per device; host code may not use the symbol itself as an address).
-int noalloc_scratch(double** out)
+// Device address of the scratch array for the current device (host code may not
+// use the symbol itself as an address).  Outside stream capture the address is
+// looked up on every call, so a device reset (which unloads the module) is
+// followed by the new address; while `st` is capturing, the address cached by
+// an earlier uncaptured call on this device is used.
+int noalloc_scratch(cudaStream_t st, double** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PAMD_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return PAMD_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return PAMD_ERR_CUDA;
         g_noalloc_ptr[dev] = static_cast<double*>(p);
     }
+    if (!g_noalloc_ptr[dev]) return PAMD_ERR_CUDA;  // first call on this device inside a capture
     *out = g_noalloc_ptr[dev];
     return PAMD_OK;
 }
@@ -91,14 +98,17 @@ __global__ void ho_noalloc_finalize(const double* __restrict__ partials, int slo
     if (lane == 0) S[chain0 + c] = v * scale;
 }
 
+// Device (or managed) memory of the current device.
 bool device_ptr(const void* p)
 {
     cudaPointerAttributes a;
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    int dev = -1;
+    if (!p || cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 template <typename R>
@@ -106,6 +116,17 @@ int run_noalloc(const pamd_problem* p, const R* pos, double* S, R* grad, double*
                 cudaStream_t st)
 {
     const double a = p->beta * p->D * p->dt, ginv = 1.0 / (2.0 * p->D * p->dt);
+    // Shared-memory attribute for the largest system, set before anything is
+    // enqueued, so that a failure leaves every output untouched.
+    size_t smem_max = 0;
+    for (int q = 0; q < p->n_systems; ++q)
+        smem_max = std::max(smem_max, sizeof(R) * (size_t)(pamd::kElemChunk +
+                                                           2 * p->systems[q].dim * p->systems[q].n_particles));
+    auto kern = ho_noalloc_kernel<R>;
+    if (smem_max > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) !=
+            cudaSuccess)
+        return PAMD_ERR_CUDA;
     int slot = 0, chain0 = 0;
     for (int q = 0; q < p->n_systems; ++q) {
         const pamd_system& s = p->systems[q];
@@ -113,11 +134,6 @@ int run_noalloc(const pamd_problem* p, const R* pos, double* S, R* grad, double*
         const int chain_len = (s.n_steps + 1) * sz;
         const int chunks = (chain_len + pamd::kElemChunk - 1) / pamd::kElemChunk;
         const size_t smem = sizeof(R) * (size_t)(pamd::kElemChunk + 2 * sz);
-        auto kern = ho_noalloc_kernel<R>;
-        if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-            return PAMD_ERR_CUDA;
         kern<<<dim3(chunks, s.n_chains), pamd::kElemThreads, smem, st>>>(
             pos, grad, scratch, slot, s.pos_offset, sz, chain_len, (R)(a * s.pot.k), (R)ginv);
         if (cudaGetLastError() != cudaSuccess) return PAMD_ERR_CUDA;
@@ -147,16 +163,17 @@ extern "C" int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void*
             s.dim > 3 || s.n_chains < 1 || s.pos_offset < 0)
             return PAMD_ERR_ARG;
         if (s.dim * s.n_particles > 8192) return PAMD_ERR_UNSUPPORTED;
+        if (s.n_chains > 65535) return PAMD_ERR_UNSUPPORTED;  // one grid row per chain
         const long long chain_len = (long long)(s.n_steps + 1) * s.dim * s.n_particles;
         if (chain_len >= (1LL << 31)) return PAMD_ERR_UNSUPPORTED;
         blocks += (long long)s.n_chains * ((chain_len + pamd::kElemChunk - 1) / pamd::kElemChunk);
     }
     if (blocks > kNoallocMaxBlocks) return PAMD_ERR_UNSUPPORTED;  // scratch array too small
     if (!device_ptr(pos) || !device_ptr(S) || !device_ptr(grad)) return PAMD_ERR_ARG;
-    double* scratch = nullptr;
-    int rc = noalloc_scratch(&scratch);
-    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(st, &scratch);
+    if (rc) return rc;
     if (prob->precision == PAMD_FP64)
         return run_noalloc<double>(prob, (const double*)pos, S, (double*)grad, scratch, st);
     return run_noalloc<float>(prob, (const float*)pos, S, (float*)grad, scratch, st);

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <functional>
 #include <type_traits>
 #include <map>
 #include <memory>
@@ -58,12 +59,18 @@ struct SysInfo {
     int n_tiles = 0;
 };
 
+// Buffers and update count of a captured update graph.  Compared field by field:
+// the struct has padding after n_updates, which a byte comparison would read.
 struct GraphKey {
     const void *pos, *grad, *S, *nacc, *la;
     int n_updates;
     bool operator<(const GraphKey& o) const
     {
-        return std::memcmp(this, &o, sizeof(GraphKey)) < 0;
+        const void* a[5] = {pos, grad, S, nacc, la};
+        const void* b[5] = {o.pos, o.grad, o.S, o.nacc, o.la};
+        for (int q = 0; q < 5; ++q)
+            if (a[q] != b[q]) return std::less<const void*>()(a[q], b[q]);
+        return n_updates < o.n_updates;
     }
 };
 
@@ -837,6 +844,16 @@ int pamd_release_cache(void)
     std::lock_guard<std::mutex> lk(g_mutex);
     cudaDeviceSynchronize();
     g_plans.clear();
+    return PAMD_OK;
+}
+
+int pamd_cache_stats(int* n_plans, int* n_graphs)
+{
+    std::lock_guard<std::mutex> lk(g_mutex);
+    int g = 0;
+    for (auto& kv : g_plans) g += (int)kv.second->graphs.size();
+    if (n_plans) *n_plans = (int)g_plans.size();
+    if (n_graphs) *n_graphs = g;
     return PAMD_OK;
 }
 

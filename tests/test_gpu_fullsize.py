@@ -35,7 +35,7 @@ def _problem(pamd, w, precision="fp32"):
                         precision=precision)
 
 
-def test_ho3d_full_size(pamd):
+def test_ho3d_full_size(pamd, parity_report):
     """3D oscillator, T = 2^20, 64 chains: every chain's S and gradient."""
     w = inputs.workload("ho3d")
     spec = w.systems[0]
@@ -56,14 +56,18 @@ def test_ho3d_full_size(pamd):
     for b in range(spec.n_chains):
         So, go = oracle.action_grad(pot, paths[b].astype(np.float64), w.D, w.beta, w.dt,
                                     nthreads=nth)
-        assert abs(S[b] - So) <= 1e-5 * So, b
+        es = abs(S[b] - So) / So
+        assert es <= 1e-5, b
+        parity_report.record("ho3d", "test_ho3d_full_size", S_rel=es)
         if b % 8 == 0:
             gb = prob.view(g, 0)[b].double().cpu().numpy()
-            assert rel(gb, go) <= 1e-5
-            assert np.abs(gb - go).max() <= 1e-5 * np.abs(go).max()
+            eg, em = rel(gb, go), np.abs(gb - go).max() / np.abs(go).max()
+            assert eg <= 1e-5 and em <= 1e-5
+            parity_report.record("ho3d", "test_ho3d_full_size", grad_rel_2norm=eg,
+                                 grad_rel_maxabs=em)
 
 
-def test_lj500_full_size(pamd):
+def test_lj500_full_size(pamd, parity_report):
     """LJ N = 500, T = 16384, 8 chains (oracle Euler-Maruyama start paths): every
     chain's S, and the gradient at 48 sampled slices per chain, incl. both ends."""
     w = inputs.workload("lj500")
@@ -84,16 +88,20 @@ def test_lj500_full_size(pamd):
     rng = inputs.rng(123)
     for b in range(spec.n_chains):
         So = oracle.action_grad(pot, paths[b], w.D, w.beta, w.dt, grad=False, nthreads=nth)
-        assert abs(S[b] - So) <= 1e-5 * So, (b, S[b], So)
+        es = abs(S[b] - So) / So
+        assert es <= 1e-5, (b, S[b], So)
         ts = np.unique(np.concatenate([[0, 1, spec.T - 1, spec.T, 31, 32, 33],
                                        rng.integers(0, spec.T + 1, 41)]))
         go = oracle.grad_slices(pot, paths[b], w.D, w.beta, w.dt, ts)
         gk = gv[b, torch.from_numpy(ts).long()].double().cpu().numpy()
-        assert rel(gk, go) <= 1e-5, b
-        assert np.abs(gk - go).max() <= 1e-5 * np.abs(go).max(), b
+        eg, em = rel(gk, go), np.abs(gk - go).max() / np.abs(go).max()
+        assert eg <= 1e-5 and em <= 1e-5, b
+        parity_report.record("lj500", "test_lj500_full_size (S of every chain; gradient at "
+                             "48 sampled slices per chain)", S_rel=es, grad_rel_2norm=eg,
+                             grad_rel_maxabs=em)
 
 
-def test_lj108_full_size(pamd):
+def test_lj108_full_size(pamd, parity_report):
     """LJ N = 108, T = 4096: complete S and gradient."""
     w = inputs.workload("lj108")
     spec = w.systems[0]
@@ -107,13 +115,15 @@ def test_lj108_full_size(pamd):
     S, g = pamd.action_grad(prob, buf)
     torch.cuda.synchronize()
     So, go = oracle.action_grad(pot, paths[0], w.D, w.beta, w.dt, nthreads=oracle.max_threads())
-    assert abs(S[0].item() - So) <= 1e-5 * So
+    es = abs(S[0].item() - So) / So
     gk = prob.view(g, 0)[0].double().cpu().numpy()
-    assert rel(gk, go) <= 1e-5
-    assert np.abs(gk - go).max() <= 1e-5 * np.abs(go).max()
+    eg, em = rel(gk, go), np.abs(gk - go).max() / np.abs(go).max()
+    assert es <= 1e-5 and eg <= 1e-5 and em <= 1e-5
+    parity_report.record("lj108", "test_lj108_full_size", S_rel=es, grad_rel_2norm=eg,
+                         grad_rel_maxabs=em)
 
 
-def test_ragged_full_size(pamd):
+def test_ragged_full_size(pamd, parity_report):
     """32 LJ systems of N in [64, 864], T in [1024, 32768], one persistent launch:
     the Euler-Maruyama invariant on every chain (paths from the library's own
     Euler-Maruyama with Philox noise), and oracle parity on three systems whose
@@ -133,6 +143,8 @@ def test_ragged_full_size(pamd):
         half = 0.5 * float((z ** 2).sum())
         # residuals equal sqrt(2 D dt) xi up to the FP32 rounding of the stored slices
         assert abs(S[c] - half) <= 1e-4 * half, (q, S[c], half)
+        parity_report.record("ragged", "test_ragged_full_size (Euler-Maruyama invariant, all "
+                             "32 systems)", S_vs_invariant_rel=abs(S[c] - half) / half)
     # oracle parity on the three shortest systems, paths generated by the oracle
     order = sorted(range(len(w.systems)), key=lambda q: w.systems[q].T * w.systems[q].N)[:3]
     nth = oracle.max_threads()
@@ -151,14 +163,19 @@ def test_ragged_full_size(pamd):
     for q, (pot, p) in refs.items():
         s = w.systems[q]
         So = oracle.action_grad(pot, p[0], w.D, w.beta, w.dt, grad=False, nthreads=nth)
-        assert abs(S[prob.chain0[q]] - So) <= 1e-5 * So
+        es = abs(S[prob.chain0[q]] - So) / So
+        assert es <= 1e-5
         ts = np.array([0, 1, s.T // 2, s.T - 1, s.T])
         go = oracle.grad_slices(pot, p[0], w.D, w.beta, w.dt, ts)
         gk = prob.view(g, q)[0, torch.from_numpy(ts).long()].double().cpu().numpy()
-        assert rel(gk, go) <= 1e-5
+        eg, em = rel(gk, go), np.abs(gk - go).max() / np.abs(go).max()
+        assert eg <= 1e-5 and em <= 1e-5
+        parity_report.record("ragged", "test_ragged_full_size (oracle on three systems; "
+                             "gradient at 5 slices)", S_rel=es, grad_rel_2norm=eg,
+                             grad_rel_maxabs=em)
 
 
-def test_ho1d_thousand_updates_fp64(pamd):
+def test_ho1d_thousand_updates_fp64(pamd, parity_report):
     """1D oscillator, T = 1024, plain FP64: 1000 seeded path updates with the
     noise and uniforms passed in, against the oracle's MALA on the same draws."""
     w = inputs.workload("ho1d")
@@ -193,5 +210,61 @@ def test_ho1d_thousand_updates_fp64(pamd):
     assert int(nacc.item()) == acc_o
     assert 100 < acc_o <= 1000
     got = prob.view(buf, 0)[0].cpu().numpy()
-    assert np.abs(got - x).max() <= 1e-10 * max(1.0, np.abs(x).max())
+    ep = np.abs(got - x).max() / max(1.0, np.abs(x).max())
+    assert ep <= 1e-10
     assert abs(S.item() - So) <= 1e-10 * So
+    gk = prob.view(g, 0)[0].cpu().numpy()
+    parity_report.record("ho1d", "test_ho1d_thousand_updates_fp64 (after 1000 updates)",
+                         path_after_1000_updates_maxabs=ep, S_after_1000_updates_rel=abs(S.item() - So) / So,
+                         grad_after_1000_updates_rel_2norm=rel(gk, go))
+
+
+def test_lj108_autograd_finite_differences_full_size(pamd, parity_report):
+    """LJ N = 108, T = 4096 through PamdAction (torch.autograd.Function): the
+    backward (the hand-written adjoint) against central finite differences of the
+    action with h = 1e-3, in the plain FP64 form, along four random unit
+    directions of the whole path; the single-precision gradient through the same
+    Function against the FP64 one."""
+    w = inputs.workload("lj108")
+    spec = w.systems[0]
+    pot = oracle_potential(spec)
+    x0 = inputs.initial_positions(spec, 1)
+    xi = inputs.euler_noise(spec, w.seed)
+    paths = oracle.euler_batch(pot, x0, xi, w.D, w.beta, w.dt, store_f32=True)
+    prob = _problem(pamd, w, "fp64")
+    buf = prob.empty("cuda")
+    prob.view(buf, 0).copy_(torch.from_numpy(paths))
+    x = buf.clone().requires_grad_(True)
+    S = pamd.PamdAction.apply(x, prob)
+    S.sum().backward()
+    g = x.grad.detach()
+    rng = inputs.rng(4096)
+    hh = 1e-3
+    worst = 0.0
+    for _ in range(4):
+        v = torch.from_numpy(rng.standard_normal(prob.span)).cuda()
+        v /= v.norm()
+        Sp = pamd.action(prob, (buf + hh * v).contiguous())
+        Sm = pamd.action(prob, (buf - hh * v).contiguous())
+        fd = float((Sp - Sm).sum()) / (2 * hh)
+        an = float((g * v).sum())
+        err = abs(fd - an) / (abs(an) + 1e-3 * float(g.norm()))
+        worst = max(worst, err)
+        assert err <= 1e-4, (fd, an)
+    # the FP64 adjoint itself against the oracle's gradient
+    So, go = oracle.action_grad(pot, paths[0], w.D, w.beta, w.dt, nthreads=oracle.max_threads())
+    e64 = rel(prob.view(g, 0)[0].cpu().numpy(), go)
+    assert e64 <= 1e-12 and abs(S.item() - So) <= 1e-12 * So
+    # float32 positions through the same Function: gradient against the FP64 one
+    p32 = _problem(pamd, w, "fp32")
+    b32 = p32.empty("cuda")
+    p32.view(b32, 0).copy_(torch.from_numpy(paths).float())
+    b32.requires_grad_(True)
+    S32 = pamd.PamdAction.apply(b32, p32)
+    S32.sum().backward()
+    e32 = rel(p32.view(b32.grad, 0)[0].double().cpu().numpy(), go)
+    assert e32 <= 1e-5 and abs(S32.item() - So) <= 1e-5 * So
+    parity_report.record("lj108", "test_lj108_autograd_finite_differences_full_size",
+                         fd_vs_adjoint_rel=worst, fp64_grad_rel_2norm=e64,
+                         fp64_S_rel=abs(S.item() - So) / So,
+                         autograd_fp32_grad_rel_2norm=e32)

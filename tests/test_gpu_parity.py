@@ -43,7 +43,7 @@ def _upload(pamd, prob, paths, device="cuda"):
 def _check_against_oracle(w, prob, paths, S, g, tol_rel, nthreads=8):
     S = S.cpu().numpy()
     g = g.cpu()
-    worst = (0.0, 0.0)
+    worst = (0.0, 0.0, 0.0)
     for q, spec in enumerate(w.systems):
         pot = oracle_potential(spec)
         gq = prob.view(g, q).double().numpy()
@@ -56,19 +56,21 @@ def _check_against_oracle(w, prob, paths, S, g, tol_rel, nthreads=8):
             assert es <= tol_rel, (q, b, es)
             assert eg <= tol_rel, (q, b, eg)
             assert emax <= tol_rel, (q, b, emax)
-            worst = (max(worst[0], es), max(worst[1], eg))
+            worst = (max(worst[0], es), max(worst[1], eg), max(worst[2], emax))
     return worst
 
 
 @pytest.mark.parametrize("name", ["ho3d", "lj108", "lj500", "ragged"])
-def test_fp32_action_grad_matches_oracle(pamd, name):
+def test_fp32_action_grad_matches_oracle(pamd, parity_report, name):
     w = inputs.workload(name, "small")
     paths = start_paths(w, "fp32")
     prob = _problem(pamd, w, "fp32")
     buf = _upload(pamd, prob, paths)
     S, g = pamd.action_grad(prob, buf)
     torch.cuda.synchronize()
-    _check_against_oracle(w, prob, paths, S, g, 1e-5)
+    es, eg, em = _check_against_oracle(w, prob, paths, S, g, 1e-5)
+    parity_report.record(f"{name}_small", "test_fp32_action_grad_matches_oracle", S_rel=es,
+                         grad_rel_2norm=eg, grad_rel_maxabs=em)
     # action-only entry point gives the same S
     S2 = pamd.action(prob, buf)
     torch.cuda.synchronize()
@@ -77,14 +79,16 @@ def test_fp32_action_grad_matches_oracle(pamd, name):
 
 @pytest.mark.parametrize("name,one", [("ho1d", True), ("ho1d", False), ("lj108", True),
                                       ("ragged", False)])
-def test_fp64_plain_matches_oracle(pamd, name, one):
+def test_fp64_plain_matches_oracle(pamd, parity_report, name, one):
     w = inputs.workload(name, "small")
     paths = start_paths(w, "fp64")
     prob = _problem(pamd, w, "fp64", one=one)
     buf = _upload(pamd, prob, paths)
     S, g = pamd.action_grad(prob, buf)
     torch.cuda.synchronize()
-    _check_against_oracle(w, prob, paths, S, g, 1e-12)
+    es, eg, em = _check_against_oracle(w, prob, paths, S, g, 1e-12)
+    parity_report.record(f"{name}_small_fp64", "test_fp64_plain_matches_oracle", S_rel=es,
+                         grad_rel_2norm=eg, grad_rel_maxabs=em)
 
 
 def test_edge_cases_tiny_paths(pamd):
@@ -483,3 +487,126 @@ def test_checkpoint_resume_is_bitwise_identical(pamd, tmp_path):
     assert torch.equal(prob.view(a.pos, 0), prob.view(c.pos, 0))
     assert torch.equal(a.S, c.S) and torch.equal(a.n_accepted, c.n_accepted)
     assert torch.equal(prob.view(a.grad, 0), prob.view(c.grad, 0))
+
+
+def test_update_graph_is_captured_once(pamd):
+    """Repeated multi-update calls on the same buffers replay one cached graph: the
+    cache must not grow call after call (the graph key compares its fields, not the
+    bytes of a padded struct)."""
+    w = inputs.workload("lj108", "small")
+    paths = start_paths(w, "fp32")
+    pamd.release_cache()
+    prob = _problem(pamd, w, "fp32")
+    buf = _upload(pamd, prob, paths)
+    S, g = pamd.action_grad(prob, buf)
+    nacc = torch.zeros(prob.n_chains, dtype=torch.int32, device="cuda")
+    for rep in range(4):
+        pamd.path_update(prob, buf, g, S, 1e-6, n_updates=3, seed=3, counter=10 * rep,
+                         n_accepted=nacc)
+    torch.cuda.synchronize()
+    n_plans, n_graphs = pamd.cache_stats()
+    assert (n_plans, n_graphs) == (1, 1)
+    pamd.path_update(prob, buf, g, S, 1e-6, n_updates=2, seed=3, counter=99, n_accepted=nacc)
+    torch.cuda.synchronize()
+    assert pamd.cache_stats() == (1, 2)
+
+
+@pytest.mark.parametrize("name", ["lj500", "ragged"])
+def test_pipelined_gradient_pass_equals_two_pass_form(pamd, name):
+    """The pipelined gradient walk (the Hessian-vector product of one step pair
+    interleaved with the force of the next) only reorders independent arithmetic:
+    S and the gradient are bitwise those of the two-pass form."""
+    import os
+    w = inputs.workload(name, "small")
+    paths = start_paths(w, "fp32")
+    outs = []
+    try:
+        for no_pipe in (False, True):
+            if no_pipe:
+                os.environ["PAMD_LJ_NO_PIPE"] = "1"
+            pamd.release_cache()
+            prob = _problem(pamd, w, "fp32")
+            buf = _upload(pamd, prob, paths)
+            S, g = pamd.action_grad(prob, buf)
+            torch.cuda.synchronize()
+            outs.append((S.cpu(), g.cpu()))
+    finally:
+        os.environ.pop("PAMD_LJ_NO_PIPE", None)
+        pamd.release_cache()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("precision,n_updates", [("fp64", 8), ("fp32", 6)])
+def test_ragged_path_updates_match_oracle_step_by_step(pamd, parity_report, precision,
+                                                       n_updates):
+    """A ragged batch of five LJ systems through successive pamd_path_update calls
+    with explicit noise and log uniforms: at every step each chain's log alpha,
+    accept decision, updated path, action and gradient agree with the oracle's MALA
+    step (oracle.mala_step) started from the library's current path.  The uniform
+    of a chain is redrawn when it falls within twice the stated agreement of log
+    alpha (1e-9 in FP64; 5e-3 in FP32, where each side rounds the proposal to
+    float), relative to 1 + |log alpha|, so that every decision is determined."""
+    w = inputs.workload("ragged", "small")
+    h = 2e-7
+    f32 = precision == "fp32"
+    paths = start_paths(w, precision)
+    prob = _problem(pamd, w, precision)
+    buf = _upload(pamd, prob, paths)
+    S, g = pamd.action_grad(prob, buf)
+    pots = [oracle_potential(s) for s in w.systems]
+    rng = inputs.rng(2024 + n_updates)
+    nacc = torch.zeros(prob.n_chains, dtype=torch.int32, device="cuda")
+    la = torch.zeros(prob.n_chains, dtype=torch.float64, device="cuda")
+    tol_la = 5e-3 if f32 else 1e-9
+    margin = 2 * tol_la
+    worst = {"log_alpha_abs": 0.0, "path_maxabs": 0.0, "S_rel": 0.0, "grad_rel_2norm": 0.0}
+    n_acc = 0
+    for k in range(n_updates):
+        x = [prob.view(buf, q).cpu().double().numpy() for q in range(len(w.systems))]
+        eta, logu, ref = [], np.zeros(prob.n_chains), {}
+        for q, s in enumerate(w.systems):
+            e = rng.standard_normal(x[q].shape)
+            if f32:
+                e = e.astype(np.float32).astype(np.float64)
+            eta.append(e)
+            for b in range(s.n_chains):
+                c = prob.chain0[q] + b
+                So, go = oracle.action_grad(pots[q], x[q][b], w.D, w.beta, w.dt, nthreads=8)
+                lu = math.log(rng.random())
+                r = oracle.mala_step(pots[q], x[q][b], So, go, e[b], lu, h, w.D, w.beta, w.dt,
+                                     store_f32=f32, nthreads=8)
+                # log alpha does not depend on u: redraw u until the decision is clear
+                while abs(lu - r["log_alpha"]) <= margin * (1 + abs(r["log_alpha"])):
+                    lu = math.log(rng.random())
+                logu[c] = lu
+                ref[c] = (q, b, lu < r["log_alpha"], r)
+        nbuf = _upload(pamd, prob, eta)
+        pamd.path_update(prob, buf, g, S, h, 1, noise=nbuf, log_u=torch.from_numpy(logu).cuda(),
+                         n_accepted=nacc, log_alpha=la)
+        torch.cuda.synchronize()
+        la_k, S_k, g_k = la.cpu().numpy(), S.cpu().numpy(), g.cpu()
+        for c, (q, b, accepted, r) in ref.items():
+            d_la = abs(la_k[c] - r["log_alpha"])
+            assert d_la <= tol_la * (1 + abs(r["log_alpha"])), (k, c, la_k[c], r["log_alpha"])
+            got = prob.view(buf, q)[b].cpu().double().numpy()
+            expect = r["prop"] if accepted else x[q][b]
+            ep = np.abs(got - expect).max()
+            lim = (4 * np.spacing(np.float32(np.abs(expect).max())) if f32
+                   else 1e-12 * max(1.0, np.abs(expect).max()))
+            assert ep <= lim, (k, c, accepted, ep)
+            # cached action and gradient of the updated path against the oracle's
+            So, go = oracle.action_grad(pots[q], got, w.D, w.beta, w.dt, nthreads=8)
+            tol = 1e-5 if f32 else 1e-12
+            es = abs(S_k[c] - So) / So
+            eg = rel(prob.view(g_k, q)[b].double().numpy(), go)
+            assert es <= tol and eg <= tol, (k, c, es, eg)
+            n_acc += int(accepted)
+            worst["log_alpha_abs"] = max(worst["log_alpha_abs"], d_la)
+            worst["path_maxabs"] = max(worst["path_maxabs"], ep)
+            worst["S_rel"] = max(worst["S_rel"], es)
+            worst["grad_rel_2norm"] = max(worst["grad_rel_2norm"], eg)
+    assert int(nacc.sum()) == n_acc and n_acc > 0
+    parity_report.record(f"ragged_updates_{precision}",
+                         f"test_ragged_path_updates_match_oracle_step_by_step ({n_updates} "
+                         f"updates, 5 systems)", **worst)
