@@ -118,32 +118,41 @@ struct SmemP {
 
 // Packed constants of one system (built per item from the per-system table).
 struct K2 {
-    float2 nL, iL, mag, nmag, c1, c2, c3, duc, m1, m7;
-    float rc2, rcm, a, ginv;
+    float2 nL, iL, mag, nmag, c12, nc1, c8, nc23, duc, nduc;
+    float rc2, rcm, a, ginv, hb, iLs;
     __device__ explicit K2(const LJK<float>& k)
     {
         nL = pk(-k.L);
         iL = pk(k.iL);
         mag = pk(12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
         nmag = pk(-12582912.0f);
-        c1 = pk(k.c1);
-        c2 = pk(k.c2);
-        c3 = pk(k.c3);
+        c12 = pk(k.c12);
+        nc1 = pk(k.nc1);
+        c8 = pk(k.c8);
+        nc23 = pk(k.nc23);
         duc = pk(k.duc);
-        m1 = pk(-1.0f);
-        m7 = pk(-7.0f);
+        nduc = pk(-k.duc);
         rc2 = k.rc2;
         rcm = k.rcm;
         a = k.a;
         ginv = k.ginv;
+        hb = k.hb;
+        iLs = k.iL;
     }
 };
 
-// Pair vector and r^2 of (step a, step b) by the single-precision minimum-image
-// rule  d = x_i - x_j;  d = fma(-L, round(d * (1/L)), d);  r2 = fma(dz,dz,fma(dy,dy,dx*dx)),
-// with r^2 = +inf for a half outside the cutoff.
-__device__ __forceinline__ float2 pair_geom(float2 xi, float2 yi, float2 zi, float4 pxy, float2 pz,
-                                            const K2& k, float2& dx, float2& dy, float2& dz)
+// Minimum-image shift of one pair-vector component, round(d / L), by the same
+// single-precision rule as the packed form below.
+__device__ __forceinline__ float image_shift(float d, const K2& k)
+{
+    return __fadd_rn(__fmaf_rn(d, k.iLs, 12582912.0f), -12582912.0f);
+}
+
+// Pair vector d = x_i - x_j of (step a, step b) by the single-precision
+// minimum-image rule  d = x_i - x_j;  d = fma(-L, round(d * (1/L)), d),  the shift
+// rounded for each step.
+__device__ __forceinline__ void pair_vec(float2 xi, float2 yi, float2 zi, float4 pxy, float2 pz,
+                                         const K2& k, float2& dx, float2& dy, float2& dz)
 {
     dx = sub2(xi, pk(pxy.x, pxy.y));
     dy = sub2(yi, pk(pxy.z, pxy.w));
@@ -151,6 +160,55 @@ __device__ __forceinline__ float2 pair_geom(float2 xi, float2 yi, float2 zi, flo
     dx = fma2(k.nL, add2(fma2(dx, k.iL, k.mag), k.nmag), dx);
     dy = fma2(k.nL, add2(fma2(dy, k.iL, k.mag), k.nmag), dy);
     dz = fma2(k.nL, add2(fma2(dz, k.iL, k.mag), k.nmag), dz);
+}
+
+// The same rule with the shift of step a applied to both steps; the shifts are
+// returned for reuse.  Within a window whose particles all stay within delta_max
+// of the reference, a pair inside the cutoff at any of its slices has one
+// nearest image whenever rc + 4 delta_max < L/2, and the shift rounded at any
+// slice is that image's: the result is then bitwise that of pair_vec (a pair
+// outside the cutoff stays outside, since the rounded shift gives the nearest
+// image of each component).
+__device__ __forceinline__ void pair_vec_shift(float2 xi, float2 yi, float2 zi, float4 pxy, float2 pz,
+                                               const K2& k, float2& dx, float2& dy, float2& dz,
+                                               float& sx, float& sy, float& sz)
+{
+    dx = sub2(xi, pk(pxy.x, pxy.y));
+    dy = sub2(yi, pk(pxy.z, pxy.w));
+    dz = sub2(zi, pz);
+    sx = image_shift(dx.x, k);
+    sy = image_shift(dy.x, k);
+    sz = image_shift(dz.x, k);
+    dx = fma2(k.nL, pk(sx), dx);
+    dy = fma2(k.nL, pk(sy), dy);
+    dz = fma2(k.nL, pk(sz), dz);
+}
+
+// ... with shifts already known (from another pair of slices of the same window).
+__device__ __forceinline__ void pair_vec_given(float2 xi, float2 yi, float2 zi, float4 pxy, float2 pz,
+                                               const K2& k, float sx, float sy, float sz, float2& dx,
+                                               float2& dy, float2& dz)
+{
+    dx = fma2(k.nL, pk(sx), sub2(xi, pk(pxy.x, pxy.y)));
+    dy = fma2(k.nL, pk(sy), sub2(yi, pk(pxy.z, pxy.w)));
+    dz = fma2(k.nL, pk(sz), sub2(zi, pz));
+}
+
+template <bool SK>
+__device__ __forceinline__ void pair_vec_sel(float2 xi, float2 yi, float2 zi, float4 pxy, float2 pz,
+                                             const K2& k, float2& dx, float2& dy, float2& dz)
+{
+    if (SK) {
+        float sx, sy, sz;
+        pair_vec_shift(xi, yi, zi, pxy, pz, k, dx, dy, dz, sx, sy, sz);
+    } else {
+        pair_vec(xi, yi, zi, pxy, pz, k, dx, dy, dz);
+    }
+}
+
+// r^2 = fma(dz,dz,fma(dy,dy,dx*dx)), +inf for a half outside the cutoff.
+__device__ __forceinline__ float2 pair_r2(float2 dx, float2 dy, float2 dz, const K2& k)
+{
     float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
     const float inf = __int_as_float(0x7f800000);
     r2.x = r2.x <= k.rc2 ? r2.x : inf;
@@ -158,15 +216,38 @@ __device__ __forceinline__ float2 pair_geom(float2 xi, float2 yi, float2 zi, flo
     return r2;
 }
 
-// -U'(r)/r from r^2, with w = ir2 u and ir6 for the Hessian coefficient.
-__device__ __forceinline__ float2 pair_fs(float2 r2, const K2& k, float2& w, float2& ir2,
-                                          float2& ir6)
+// fs = -U'(r)/r = ir8 (c12 ir6 - c1) + u'(rc)/r, with 1/r, r^-2, r^-6, r^-8 for the
+// Hessian coefficient.  r^2 = +inf gives exact zeros.
+__device__ __forceinline__ float2 pair_fs(float2 r2, const K2& k, float2& ri, float2& ir2,
+                                          float2& ir6, float2& ir8)
 {
-    const float2 ri = pk(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    ri = pk(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
     ir2 = mul2(ri, ri);
-    ir6 = mul2(mul2(ir2, ir2), ir2);
-    w = mul2(ir2, mul2(k.c1, ir6));
-    return fma2(w, fma2(k.c2, ir6, k.m1), mul2(k.duc, ri));
+    const float2 ir4 = mul2(ir2, ir2);
+    ir6 = mul2(ir4, ir2);
+    ir8 = mul2(ir4, ir4);
+    return fma2(ir8, fma2(k.c12, ir6, k.nc1), mul2(k.duc, ri));
+}
+
+// -(U''(r) - U'(r)/r) / r^2 = [ir8 (8 c1 - c1 (c2 + c3) ir6) - u'(rc)/r] r^-2.
+__device__ __forceinline__ float2 pair_nbc(float2 ri, float2 ir2, float2 ir6, float2 ir8, const K2& k)
+{
+    return mul2(fma2(ir8, fma2(k.nc23, ir6, k.c8), mul2(k.nduc, ri)), ir2);
+}
+
+// One pair's Hessian-vector term, added to h:  (H v)_i gets
+//   sum_j [-fs v_ij + Bc (d . v_ij) d] = sum_j [fs w + (-Bc) (d . w) d],  w = v_j - v_i.
+__device__ __forceinline__ void hvp_term(float2 dx, float2 dy, float2 dz, float2 fs, float2 nbc,
+                                         float4 vj, float2 vjz, float2 vix, float2 viy, float2 viz,
+                                         float2& hx, float2& hy, float2& hz)
+{
+    const float2 wx = sub2(pk(vj.x, vj.y), vix);
+    const float2 wy = sub2(pk(vj.z, vj.w), viy);
+    const float2 wz = sub2(vjz, viz);
+    const float2 bd = mul2(nbc, fma2(dz, wz, fma2(dy, wy, mul2(dx, wx))));
+    hx = fma2(fs, wx, fma2(bd, dx, hx));
+    hy = fma2(fs, wy, fma2(bd, dy, hy));
+    hz = fma2(fs, wz, fma2(bd, dz, hz));
 }
 
 // The particle a thread works for, its list, and the candidate loop.
@@ -324,6 +405,8 @@ struct PairList {
     }
 
     // F(x_a), F(x_b) of particle i (complete in every thread of the group).
+    // SK: the window allows one image shift per pair (pair_vec_shift).
+    template <bool SK>
     __device__ void force(const Smem<NMAX>& P, const K2& k, float2& fx, float2& fy, float2& fz) const
     {
         fx = fy = fz = pk(0.0f);
@@ -331,9 +414,9 @@ struct PairList {
             const float4 pxy = P.xy(8 * i);
             const float2 xi = pk(pxy.x, pxy.y), yi = pk(pxy.z, pxy.w), zi = P.z(8 * i);
             for_each_candidate([&](int o8) {
-                float2 dx, dy, dz, w, ir2, ir6;
-                const float2 r2 = pair_geom(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
-                const float2 fs = pair_fs(r2, k, w, ir2, ir6);
+                float2 dx, dy, dz, ri, ir2, ir6, ir8;
+                pair_vec_sel<SK>(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
+                const float2 fs = pair_fs(pair_r2(dx, dy, dz, k), k, ri, ir2, ir6, ir8);
                 fx = fma2(fs, dx, fx);
                 fy = fma2(fs, dy, fy);
                 fz = fma2(fs, dz, fz);
@@ -343,6 +426,7 @@ struct PairList {
     }
 
     // (H(x_a) v_a, H(x_b) v_b) of particle i; v is the residual array, vi its own value.
+    template <bool SK>
     __device__ void hvp(const Smem<NMAX>& P, float2 vix, float2 viy, float2 viz, const K2& k,
                         float2& hx, float2& hy, float2& hz) const
     {
@@ -351,19 +435,11 @@ struct PairList {
             const float4 pxy = P.xy(8 * i);
             const float2 xi = pk(pxy.x, pxy.y), yi = pk(pxy.z, pxy.w), zi = P.z(8 * i);
             for_each_candidate([&](int o8) {
-                float2 dx, dy, dz, w, ir2, ir6;
-                const float2 r2 = pair_geom(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
-                const float2 fs = pair_fs(r2, k, w, ir2, ir6);                       // -U'/r
-                const float2 Bc = mul2(fma2(w, fma2(k.c3, ir6, k.m7), fs), ir2);     // (U''-U'/r)/r^2
-                const float2 nfs = mul2(fs, k.m1);
-                const float4 vj = P.rxy(o8);
-                const float2 vx = sub2(vix, pk(vj.x, vj.y));
-                const float2 vy = sub2(viy, pk(vj.z, vj.w));
-                const float2 vz = sub2(viz, P.rz(o8));
-                const float2 bd = mul2(Bc, fma2(dz, vz, fma2(dy, vy, mul2(dx, vx))));
-                hx = fma2(nfs, vx, fma2(bd, dx, hx));
-                hy = fma2(nfs, vy, fma2(bd, dy, hy));
-                hz = fma2(nfs, vz, fma2(bd, dz, hz));
+                float2 dx, dy, dz, ri, ir2, ir6, ir8;
+                pair_vec_sel<SK>(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
+                const float2 fs = pair_fs(pair_r2(dx, dy, dz, k), k, ri, ir2, ir6, ir8);
+                hvp_term(dx, dy, dz, fs, pair_nbc(ri, ir2, ir6, ir8, k), P.rxy(o8), P.rz(o8), vix,
+                         viy, viz, hx, hy, hz);
             });
         }
         group_sum(hx, hy, hz);
@@ -372,8 +448,11 @@ struct PairList {
     // One walk over the list for the pipelined form: the Hessian-vector product of
     // the pair in buffer hb with the residual array (DO_H) and the force of the
     // pair in buffer fb (DO_F).  Each result equals that of hvp() / force() on
-    // the same slices: the two chains of arithmetic are only interleaved.
-    template <bool DO_H, bool DO_F>
+    // the same slices: the two chains of arithmetic are only interleaved.  SK: one
+    // image shift per list entry, rounded at the first slice walked and applied to
+    // all four (the window keeps every particle within (L/2 - rc)/4 of its
+    // reference, so the shift is the nearest image's at each of them).
+    template <bool DO_H, bool DO_F, bool SK>
     __device__ void combined(const SmemP<NMAX>& P, int hb, int fb, float2 vix, float2 viy,
                              float2 viz, const K2& k, float2& hx, float2& hy, float2& hz,
                              float2& fx, float2& fy, float2& fz) const
@@ -385,25 +464,26 @@ struct PairList {
             const float4 fxy = P.xy(fb, 8 * i);
             const float2 fxi = pk(fxy.x, fxy.y), fyi = pk(fxy.z, fxy.w), fzi = P.z(fb, 8 * i);
             for_each_candidate([&](int o8) {
+                float sx = 0.0f, sy = 0.0f, sz = 0.0f;
                 if (DO_H) {
-                    float2 dx, dy, dz, w, ir2, ir6;
-                    const float2 r2 = pair_geom(hxi, hyi, hzi, P.xy(hb, o8), P.z(hb, o8), k, dx, dy, dz);
-                    const float2 fs = pair_fs(r2, k, w, ir2, ir6);
-                    const float2 Bc = mul2(fma2(w, fma2(k.c3, ir6, k.m7), fs), ir2);
-                    const float2 nfs = mul2(fs, k.m1);
-                    const float4 vj = P.rxy(o8);
-                    const float2 vx = sub2(vix, pk(vj.x, vj.y));
-                    const float2 vy = sub2(viy, pk(vj.z, vj.w));
-                    const float2 vz = sub2(viz, P.rz(o8));
-                    const float2 bd = mul2(Bc, fma2(dz, vz, fma2(dy, vy, mul2(dx, vx))));
-                    hx = fma2(nfs, vx, fma2(bd, dx, hx));
-                    hy = fma2(nfs, vy, fma2(bd, dy, hy));
-                    hz = fma2(nfs, vz, fma2(bd, dz, hz));
+                    float2 dx, dy, dz, ri, ir2, ir6, ir8;
+                    if (SK)
+                        pair_vec_shift(hxi, hyi, hzi, P.xy(hb, o8), P.z(hb, o8), k, dx, dy, dz, sx, sy, sz);
+                    else
+                        pair_vec(hxi, hyi, hzi, P.xy(hb, o8), P.z(hb, o8), k, dx, dy, dz);
+                    const float2 fs = pair_fs(pair_r2(dx, dy, dz, k), k, ri, ir2, ir6, ir8);
+                    hvp_term(dx, dy, dz, fs, pair_nbc(ri, ir2, ir6, ir8, k), P.rxy(o8), P.rz(o8),
+                             vix, viy, viz, hx, hy, hz);
                 }
                 if (DO_F) {
-                    float2 dx, dy, dz, w, ir2, ir6;
-                    const float2 r2 = pair_geom(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz);
-                    const float2 fs = pair_fs(r2, k, w, ir2, ir6);
+                    float2 dx, dy, dz, ri, ir2, ir6, ir8;
+                    if (SK && DO_H)
+                        pair_vec_given(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, sx, sy, sz, dx, dy, dz);
+                    else if (SK)
+                        pair_vec_shift(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz, sx, sy, sz);
+                    else
+                        pair_vec(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz);
+                    const float2 fs = pair_fs(pair_r2(dx, dy, dz, k), k, ri, ir2, ir6, ir8);
                     fx = fma2(fs, dx, fx);
                     fy = fma2(fs, dy, fy);
                     fz = fma2(fs, dz, fz);
@@ -420,12 +500,51 @@ __device__ __forceinline__ float sq3(float x, float y, float z)
     return __fmaf_rn(z, z, __fmaf_rn(y, y, x * x));
 }
 
+// Stage the reference of slices [lo, hi) of a chain X -- the middle slice -- with
+// each particle's margin delta = max |x_t - x_c| over them, as {x, y, z, delta},
+// and raise *dmax_bits (the bits of a non-negative float, so integer order is
+// float order) to the largest delta.  Called by every thread of the block.
+template <class SM>
+__device__ __forceinline__ void stage_reference(const SM& P, const float* __restrict__ X, int N,
+                                                int lo, int hi, int* dmax_bits)
+{
+    const int s = 3 * N;
+    const int c = lo + (hi - 1 - lo) / 2;
+    float dmax = 0.0f;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const float* A = X + n;
+        const float* C = A + (long long)c * s;
+        const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
+        float d2 = 0.0f;
+#pragma unroll 4
+        for (int t = lo; t < hi; ++t) {
+            const float* Q = A + (long long)t * s;
+            const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
+            d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
+        }
+        // delta rounded up: sqrt and the sums above are within a few ulp
+        const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
+        P.ref(8 * n) = make_float4(cx, cy, cz, delta);
+        dmax = fmaxf(dmax, delta);
+    }
+    const int m = __reduce_max_sync(0xffffffffu, __float_as_int(dmax));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(dmax_bits, m);
+}
+
+// Whether the window just staged allows one image shift per list entry (see
+// pair_vec_shift): rc + 4 delta_max below half the box (less a rounding allowance).
+__device__ __forceinline__ bool window_shared_shift(const LJSysDev<float>& S, const K2& k,
+                                                    const int* dmax_bits)
+{
+    return S.shared_shift && k.rcm + 4.0f * __int_as_float(*dmax_bits) <= k.hb;
+}
+
 // One work item: steps [t0, t1) of one chain.
 template <bool GRAD, int NMAX>
 __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<float>& S,
                                             unsigned char* smem, const float* __restrict__ pos,
                                             float* __restrict__ grad, double* __restrict__ partials,
-                                            double* red, uint32_t* outer)
+                                            double* red, uint32_t* outer, int* dmax_bits)
 {
     const int N = S.N;
     const Smem<NMAX> P{smem};
@@ -463,31 +582,11 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
     }
     __syncthreads();
 
-    // Stage the reference of slices [lo, hi) -- the middle slice -- with each
-    // particle's margin delta = max |x_t - x_c| over them, as {x, y, z, delta}.
-    auto stage = [&](int lo, int hi) {
-        const int c = lo + (hi - 1 - lo) / 2;
-        for (int n = threadIdx.x; n < N; n += blockDim.x) {
-            const float* A = X + n;
-            const float* C = A + (long long)c * s;
-            const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
-            float d2 = 0.0f;
-#pragma unroll 4
-            for (int t = lo; t < hi; ++t) {
-                const float* Q = A + (long long)t * s;
-                const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
-                d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
-            }
-            // delta rounded up: sqrt and the sums above are within a few ulp
-            const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
-            P.ref(8 * n) = make_float4(cx, cy, cz, delta);
-        }
-    };
-
     float rpx = 0.0f, rpy = 0.0f, rpz = 0.0f;  // r_{a-1}
     double acc = 0.0;
     const int W = max(2, S.window);
     int win_end = ts;  // slices [.., win_end) are covered by the current list
+    bool sk = false;   // the current window allows one image shift per entry
 
     for (int a = ts; a < t1; a += 2) {
         const int b = a + 1;
@@ -507,23 +606,29 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
 
         if (a == ts) {
             // Outer list over the item's slices [ts, t1].
-            stage(ts, t1 + 1);
+            stage_reference(P, X, N, ts, t1 + 1, dmax_bits);
             __syncthreads();
             L.build_outer(P, k);
             __syncthreads();  // the staged reference is replaced below
+            if (threadIdx.x == 0) *dmax_bits = 0;
         }
         if (b >= win_end) {
             // New window: slices [a, e) (every pair inside has b <= t1 <= T).
             const int e = min(a + W, t1 + 1);
-            stage(a, e);
+            stage_reference(P, X, N, a, e, dmax_bits);
             __syncthreads();
+            sk = window_shared_shift(S, k, dmax_bits);
             L.build(P, k);
             __syncthreads();  // the staged reference is overwritten by residuals below
+            if (threadIdx.x == 0) *dmax_bits = 0;  // read by all before the barrier above
             win_end = e;
         }
 
         float2 fx, fy, fz;
-        L.force(P, k, fx, fy, fz);
+        if (sk)
+            L.template force<true>(P, k, fx, fy, fz);
+        else
+            L.template force<false>(P, k, fx, fy, fz);
         float2 rx = pk(0.0f), ry = pk(0.0f), rz = pk(0.0f);
         if (L.active) {
             const float4 pxy = P.xy(8 * i);
@@ -545,7 +650,10 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
         if (GRAD) {
             __syncthreads();
             float2 hx, hy, hz;
-            L.hvp(P, rx, ry, rz, k, hx, hy, hz);
+            if (sk)
+                L.template hvp<true>(P, rx, ry, rz, k, hx, hy, hz);
+            else
+                L.template hvp<false>(P, rx, ry, rz, k, hx, hy, hz);
             if (lead) {
                 // g = (r_prev - r + a H r) / (2 D dt), packed over (a, b).
                 const float2 gx = mul2(fma2(pk(k.a), hx, sub2(pk(rpx, rx.x), rx)), ginv);
@@ -593,7 +701,7 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
                                                  unsigned char* smem, const float* __restrict__ pos,
                                                  float* __restrict__ grad,
                                                  double* __restrict__ partials, double* red,
-                                                 uint32_t* outer)
+                                                 uint32_t* outer, int* dmax_bits)
 {
     const int N = S.N;
     const SmemP<NMAX> P{smem};
@@ -622,34 +730,20 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
         P.xy(buf, 8 * n) = make_float4(v[0], v[1], v[2], v[3]);
         P.z(buf, 8 * n) = make_float2(v[4], v[5]);
     };
-    auto stage = [&](int lo, int hi) {
-        const int c = lo + (hi - 1 - lo) / 2;
-        for (int n = threadIdx.x; n < N; n += blockDim.x) {
-            const float* A = X + n;
-            const float* C = A + (long long)c * s;
-            const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
-            float d2 = 0.0f;
-#pragma unroll 4
-            for (int t = lo; t < hi; ++t) {
-                const float* Q = A + (long long)t * s;
-                const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
-                d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
-            }
-            const float delta = __fmaf_rn(sqrtf(d2), 1.0f + 1.0e-6f, 1.0e-6f);
-            P.ref(8 * n) = make_float4(cx, cy, cz, delta);
-        }
-    };
     const int W = max(4, S.window);
     int win_end = ts;
+    bool sk = false;  // the current window allows one image shift per entry
     // Window list covering slices up to `last` (the b slice of the later of the two
     // pairs the next walk touches), starting at slice a.
     auto ensure_window = [&](int a, int last) {
         if (last < win_end) return;
         const int e = min(a + W, t1 + 1);  // > last: last <= a + 3 <= a + W, or last <= t1
-        stage(a, e);
+        stage_reference(P, X, N, a, e, dmax_bits);
         __syncthreads();
+        sk = window_shared_shift(S, k, dmax_bits);
         L.build(P, k);
         __syncthreads();
+        if (threadIdx.x == 0) *dmax_bits = 0;  // read by all before the barrier above
         win_end = e;
     };
     // residuals of the pair starting at slice a (in buffer buf), F its force
@@ -683,10 +777,11 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     };
 
     // Item-wide outer list.
-    stage(ts, t1 + 1);
+    stage_reference(P, X, N, ts, t1 + 1, dmax_bits);
     __syncthreads();
     L.build_outer(P, k);
     __syncthreads();
+    if (threadIdx.x == 0) *dmax_bits = 0;
 
     // Pairs a = ts + 2p, p < np; buffers: pair p in buffer p & 1.
     const int np = (t1 - ts + 1) / 2;
@@ -706,8 +801,12 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     float2 rx, ry, rz;  // residuals of the current pair
     {
         float2 hx, hy, hz, fx, fy, fz;
-        L.template combined<false, true>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx, hy, hz, fx,
-                                         fy, fz);
+        if (sk)
+            L.template combined<false, true, true>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx, hy,
+                                                   hz, fx, fy, fz);
+        else
+            L.template combined<false, true, false>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx, hy,
+                                                    hz, fx, fy, fz);
         residual(0, ts, fx, fy, fz, rx, ry, rz);
         account(ts, rx, ry, rz);
     }
@@ -725,10 +824,14 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
         if (pf) fetch(a + 4, threadIdx.x, nv);
 
         float2 hx, hy, hz, fx, fy, fz;
-        if (next)
-            L.template combined<true, true>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+        if (next && sk)
+            L.template combined<true, true, true>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+        else if (next)
+            L.template combined<true, true, false>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+        else if (sk)
+            L.template combined<true, false, true>(P, cur, cur, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
         else
-            L.template combined<true, false>(P, cur, cur, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+            L.template combined<true, false, false>(P, cur, cur, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
         if (lead) {
             const float2 gx = mul2(fma2(pk(k.a), hx, sub2(pk(rpx, rx.x), rx)), ginv);
             const float2 gy = mul2(fma2(pk(k.a), hy, sub2(pk(rpy, ry.x), ry)), ginv);
@@ -784,6 +887,8 @@ __global__ void __launch_bounds__(MAXT, 1)
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ int s_item;
+    __shared__ int s_dmax;  // bits of the largest margin of the window being staged
+    if (threadIdx.x == 0) s_dmax = 0;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -794,10 +899,10 @@ __global__ void __launch_bounds__(MAXT, 1)
         const LJSysDev<float> S = systems[I.sys];
         if (GRAD && PIPE)
             paired_item_pipe<MAXT>(I, S, smem_raw, pos, grad, partials, red,
-                                   outer + (long long)blockIdx.x * outer_words);
+                                   outer + (long long)blockIdx.x * outer_words, &s_dmax);
         else
             paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red,
-                                    outer + (long long)blockIdx.x * outer_words);
+                                    outer + (long long)blockIdx.x * outer_words, &s_dmax);
     }
 }
 

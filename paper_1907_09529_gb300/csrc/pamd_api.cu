@@ -325,6 +325,9 @@ void fill_lj_sys(Plan* P, const pamd_problem* p)
         d.cap = si.tune.maxnb;
         d.window = si.tune.window;
         d.outer_cap = si.tune.outer_cap;
+        // (PAMD_LJ_PER_STEP_SHIFT=1 rounds the image shift at every slice instead; the
+        // results are bitwise the same, which a test checks)
+        d.shared_shift = std::getenv("PAMD_LJ_PER_STEP_SHIFT") == nullptr;
         LJConst c;
         c.L = si.pot.box;
         c.rc = si.pot.rc;

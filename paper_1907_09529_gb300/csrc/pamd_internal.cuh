@@ -192,6 +192,12 @@ struct LJK {
     R rcm;                   // rc plus a margin that covers rounding in window lists
     R c1, c2, c3, duc;       // 24 eps sigma^6, 2 sigma^6, 26 sigma^6, u'(rc)
     R a, ginv, sig_em;       // beta D dt, 1/(2 D dt), sqrt(2 D dt)
+    // Folded coefficients of the paired kernel, with ir8 = r^-8, ir6 = r^-6:
+    //   -U'(r)/r               = ir8 (c12 ir6 + nc1) + duc / r
+    //   -(U''(r) - U'(r)/r)/r^2 = [ir8 (c8 + nc23 ir6) - duc / r] / r^2
+    R c12, nc1, c8, nc23;    // c1 c2, -c1, 8 c1, -c1 (c2 + c3)
+    R hb;                    // half the box less a rounding allowance: one image shift
+                             // serves a window when rc + 4 max(delta) <= hb
 };
 
 template <typename R>
@@ -223,6 +229,11 @@ inline LJK<R> make_lj_consts(const LJConst& c, double sig_em)
     k.c2 = (R)(2.0 * s6);
     k.c3 = (R)(26.0 * s6);
     k.duc = (R)duc;
+    k.c12 = (R)(24.0 * c.eps * s6 * 2.0 * s6);
+    k.nc1 = (R)(-24.0 * c.eps * s6);
+    k.c8 = (R)(8.0 * 24.0 * c.eps * s6);
+    k.nc23 = (R)(-24.0 * c.eps * s6 * 28.0 * s6);
+    k.hb = (R)(0.5 * c.L * (1.0 - 1.0e-5) - 1.0e-5);
     k.a = (R)c.a;
     k.ginv = (R)c.ginv;
     k.sig_em = (R)sig_em;
@@ -239,6 +250,7 @@ struct LJSysDev {
     int cap;              // neighbour-list capacity per thread
     int window;           // steps per neighbour-list window (paired kernel)
     int outer_cap;        // outer-list capacity per thread (paired kernel, global memory)
+    int shared_shift;     // paired kernel: windows may use one image shift per list entry
     LJK<R> k;
 };
 

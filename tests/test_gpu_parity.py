@@ -514,27 +514,36 @@ def test_update_graph_is_captured_once(pamd):
 @pytest.mark.parametrize("name", ["lj500", "ragged"])
 def test_pipelined_gradient_pass_equals_two_pass_form(pamd, name):
     """The pipelined gradient walk (the Hessian-vector product of one step pair
-    interleaved with the force of the next) only reorders independent arithmetic:
-    S and the gradient are bitwise those of the two-pass form."""
+    interleaved with the force of the next) only reorders independent arithmetic,
+    and a window whose particles stay within (L/2 - rc)/4 of its reference uses the
+    image shift rounded once per list entry, which is then the shift rounded at
+    every slice: S and the gradient are bitwise the same with either form and
+    either shift rule."""
     import os
     w = inputs.workload(name, "small")
     paths = start_paths(w, "fp32")
     outs = []
     try:
-        for no_pipe in (False, True):
-            if no_pipe:
-                os.environ["PAMD_LJ_NO_PIPE"] = "1"
+        for env in ({}, {"PAMD_LJ_NO_PIPE": "1"}, {"PAMD_LJ_PER_STEP_SHIFT": "1"},
+                    {"PAMD_LJ_NO_PIPE": "1", "PAMD_LJ_PER_STEP_SHIFT": "1"}):
+            for key in ("PAMD_LJ_NO_PIPE", "PAMD_LJ_PER_STEP_SHIFT"):
+                os.environ.pop(key, None)
+            os.environ.update(env)
             pamd.release_cache()
             prob = _problem(pamd, w, "fp32")
             buf = _upload(pamd, prob, paths)
             S, g = pamd.action_grad(prob, buf)
+            S1 = pamd.action(prob, buf)
             torch.cuda.synchronize()
-            outs.append((S.cpu(), g.cpu()))
+            outs.append((S.cpu(), g.cpu(), S1.cpu()))
     finally:
-        os.environ.pop("PAMD_LJ_NO_PIPE", None)
+        for key in ("PAMD_LJ_NO_PIPE", "PAMD_LJ_PER_STEP_SHIFT"):
+            os.environ.pop(key, None)
         pamd.release_cache()
-    assert torch.equal(outs[0][0], outs[1][0])
-    assert torch.equal(outs[0][1], outs[1][1])
+    for S, g, S1 in outs[1:]:
+        assert torch.equal(outs[0][0], S)
+        assert torch.equal(outs[0][1], g)
+        assert torch.equal(outs[0][2], S1)
 
 
 @pytest.mark.parametrize("precision,n_updates", [("fp64", 8), ("fp32", 6)])
