@@ -278,6 +278,21 @@ def measure_fp32_peak(dev, stream, target_ms=60.0):
     return res
 
 
+def host_facts():
+    """CPU placement of this process (the host side of the end-to-end copies)."""
+    facts = {"cpus": os.cpu_count()}
+    try:
+        facts["cpus_allowed"] = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        pass
+    try:
+        facts["numa_nodes"] = len([d for d in os.listdir("/sys/devices/system/node")
+                                   if d.startswith("node") and d[4:].isdigit()])
+    except OSError:
+        pass
+    return facts
+
+
 def rank_seed(w, rank: int) -> int:
     """Every rank draws its own chains: the workload is replicated with a
     rank-dependent seed (weak scaling, no data exchanged between ranks)."""
@@ -547,11 +562,17 @@ def main():
         t_e2e = (time.perf_counter() - t0) / ne
         e2e_clk = e2e_clocks.stop()
         nbuf = prob.span * 4
+        from paper_1907_09529_gb300 import _lib
+        total_ms, chunks = _lib.pamd_pipeline_timeline()
         e2e = {"value": units_rank * world / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
                "d2h_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
                "ms_per_step": t_e2e * 1e3, "sm_mhz": e2e_clk.get("sm_mhz"),
-               "pinned_copy_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)}}
+               "pinned_copy_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)},
+               "pipeline": {"lanes": int(os.environ.get("PAMD_PIPE_LANES", "3")),
+                            "last_step_device_ms": round(total_ms, 3),
+                            "chunks_ms_in_updated_out": [[round(v, 3) for v in c] for c in chunks]},
+               "host": host_facts()}
 
     # The ragged workload's full path-sampling loop: 100 updates in one call, which
     # the library captures once into a CUDA graph and then replays.

@@ -157,7 +157,8 @@ int pamd_action_grad(const pamd_problem* prob, const void* pos, double* S, void*
  * a CUDA graph (cached per shape) and replayed.  With host buffers, no noise
  * and no log_u, and at least two chains, the call is pipelined over up to 8
  * chunks of chains: one chunk's buffers are copied in while earlier chunks
- * are updated and copied back (the library's own streams, ordered after the
+ * are updated (on up to three compute streams, so that several chunks' kernels
+ * share the GPU) and copied back (the library's own streams, ordered after the
  * work already queued on `stream`); the results are bitwise those of the
  * device-pointer call, and the call returns once every result is on the host. */
 int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S, double h,
@@ -347,6 +348,15 @@ const char* pamd_status_string(int status);
  * a loop that repeats a call on the same buffers must leave both unchanged.
  * Either pointer may be NULL.  Host-side; no device work. */
 int pamd_cache_stats(int* n_plans, int* n_graphs);
+
+/* Timeline of the last pamd_path_update call that was pipelined over chunks of
+ * chains (host buffers; a diagnostic, not part of the method): ms[0] is the
+ * call's device time from its start to the last copy back, then for each chunk
+ * k three times since the start: its inputs on the device, its update done,
+ * its results on the host (ms[1 + 3k + 0..2]).  Writes min(max_entries,
+ * 1 + 3 n_chunks) floats; *n_chunks (may be NULL) gets the number of chunks
+ * (0 if no pipelined call was made).  Host-side; no device work. */
+int pamd_pipeline_timeline(float* ms, int max_entries, int* n_chunks);
 
 /* Free every cached plan, workspace and graph (synchronises the device). */
 int pamd_release_cache(void);

@@ -35,7 +35,7 @@ EXPORTS = (
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
     "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate", "pamd_event",
-    "pamd_cache_stats", "pamd_fp32_fma_probe",
+    "pamd_cache_stats", "pamd_fp32_fma_probe", "pamd_pipeline_timeline",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
             "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
             "pamd_device_status": (ctypes.c_int, [_VP]),
             "pamd_cache_stats": (ctypes.c_int, [_VP, _VP]),
+            "pamd_pipeline_timeline": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
             "pamd_fp32_fma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, _VP, _VP, _VP]),
             "pamd_fragment_mc": (ctypes.c_int, [_PP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -188,6 +189,16 @@ def pamd_device_status(stream):
 
 def pamd_release_cache():
     return _call("pamd_release_cache")
+
+
+def pamd_pipeline_timeline():
+    """(total ms, [(inputs on device, update done, results on host) ms per chunk]) of
+    the last host-buffer update pipelined over chunks of chains."""
+    n = ctypes.c_int(0)
+    _call("pamd_pipeline_timeline", None, 0, ctypes.byref(n))
+    buf = (ctypes.c_float * (1 + 3 * n.value))()
+    _call("pamd_pipeline_timeline", buf, 1 + 3 * n.value, ctypes.byref(n))
+    return buf[0], [tuple(buf[1 + 3 * k:4 + 3 * k]) for k in range(n.value)]
 
 
 def pamd_cache_stats():

@@ -128,12 +128,14 @@ struct Plan {
     int* d_stage_int = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::vector<void*> allocs;
-    // paired LJ kernel: outer lists, two sets (compute lanes) of one region per CTA
+    // paired LJ kernel: outer lists, one set per compute lane of one region per CTA
     uint32_t* d_outer = nullptr;
     long long outer_words = 0;  // 32-bit words per CTA region
-    // host-buffer pipeline: copy streams, a second compute stream, events and one LJ
-    // work counter per chunk (created on first use)
-    cudaStream_t s_in = nullptr, s_out = nullptr, s_cmp = nullptr;
+    int n_lanes = 1;            // compute lanes of the host-buffer pipeline
+    // host-buffer pipeline: copy streams, the extra compute streams (lanes 1..), events
+    // and one LJ work counter per chunk (created on first use)
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaStream_t> s_cmp;
     std::vector<cudaEvent_t> events;
     int* d_chunk_counters = nullptr;
 
@@ -143,7 +145,7 @@ struct Plan {
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         if (s_in) cudaStreamDestroy(s_in);
         if (s_out) cudaStreamDestroy(s_out);
-        if (s_cmp) cudaStreamDestroy(s_cmp);
+        for (cudaStream_t c : s_cmp) cudaStreamDestroy(c);
         for (void* p : allocs) cudaFree(p);
     }
     template <typename T>
@@ -341,6 +343,21 @@ void fill_lj_sys(Plan* P, const pamd_problem* p)
     }
 }
 
+// Compute lanes (streams) of the host-buffer pipeline: chunk k is updated on lane
+// k mod lanes, so that up to `lanes` chunks' kernels share the GPU while later
+// chunks are copied in.  PAMD_PIPE_LANES overrides the default (1..4).
+constexpr int kMaxPipeLanes = 4;
+int pipeline_lanes()
+{
+    const char* e = std::getenv("PAMD_PIPE_LANES");
+    const int v = e ? std::atoi(e) : 3;
+    return std::max(1, std::min(kMaxPipeLanes, v));
+}
+
+// Timeline of the last pipelined host-buffer update (milliseconds after its start):
+// [total, then per chunk: inputs on the device, update done, results on the host].
+std::vector<float> g_last_timeline;
+
 int build_plan(const pamd_problem* p, Plan** out)
 {
     std::string key = plan_key(p);
@@ -531,8 +548,10 @@ int build_plan(const pamd_problem* p, Plan** out)
                 for (auto& si : P->sys)
                     if (si.kind == PAMD_LJ) ocap = std::max(ocap, si.tune.outer_cap);
                 P->outer_words = (long long)(ocap / 2) * NT;
+                P->n_lanes = pipeline_lanes();
                 const long long grid = std::max(P->lj_grid_grad, P->lj_grid_nograd);
-                if ((rc0 = P->alloc(&P->d_outer, sizeof(uint32_t) * 2 * grid * P->outer_words)))
+                if ((rc0 = P->alloc(&P->d_outer,
+                                    sizeof(uint32_t) * P->n_lanes * grid * P->outer_words)))
                     return rc0;
             }
             if (P->fp64)
@@ -749,13 +768,19 @@ int path_update_pipelined(const pamd_problem* prob, Plan* P, void* pos, void* gr
     if (!P->s_in) {
         PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&P->s_in, cudaStreamNonBlocking));
         PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&P->s_out, cudaStreamNonBlocking));
-        PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&P->s_cmp, cudaStreamNonBlocking));
+    }
+    while ((int)P->s_cmp.size() < P->n_lanes - 1) {
+        cudaStream_t c;
+        PAMD_CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+        P->s_cmp.push_back(c);
     }
     if (!P->d_chunk_counters && (rc = P->alloc(&P->d_chunk_counters, sizeof(int) * kMaxChunks)))
         return rc;
-    while ((int)P->events.size() < 2 * kMaxChunks + 2) {
+    // events: per chunk inputs-copied, updated, results-copied; start and end (timed,
+    // for the timeline that pamd_pipeline_timeline reports)
+    while ((int)P->events.size() < 3 * kMaxChunks + 2) {
         cudaEvent_t e;
-        PAMD_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        PAMD_CUDA_TRY(cudaEventCreate(&e));
         P->events.push_back(e);
     }
     // Element extent of each chain, and chunk boundaries balanced by elements.
@@ -778,10 +803,10 @@ int path_update_pipelined(const pamd_problem* prob, Plan* P, void* pos, void* gr
             if ((run * K >= total * k || nc - (c + 1) == K - k) && nc - (c + 1) >= K - k) cut[k++] = c + 1;
         }
     }
-    cudaEvent_t ev_start = P->events[2 * kMaxChunks], ev_fin = P->events[2 * kMaxChunks + 1];
+    cudaEvent_t ev_start = P->events[3 * kMaxChunks], ev_fin = P->events[3 * kMaxChunks + 1];
     PAMD_CUDA_TRY(cudaEventRecord(ev_start, st));  // host buffers may be written by earlier work on st
     PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_in, ev_start, 0));
-    PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_cmp, ev_start, 0));
+    for (cudaStream_t c : P->s_cmp) PAMD_CUDA_TRY(cudaStreamWaitEvent(c, ev_start, 0));
     for (int k = 0; k < K; ++k) {
         const int c0 = cut[k], c1 = cut[k + 1];
         if (c0 >= c1) continue;
@@ -795,15 +820,16 @@ int path_update_pipelined(const pamd_problem* prob, Plan* P, void* pos, void* gr
         if (hn)
             PAMD_CUDA_TRY(cudaMemcpyAsync(dnacc + c0, n_accepted + c0, sizeof(int) * (c1 - c0),
                                           cudaMemcpyHostToDevice, P->s_in));
-        cudaStream_t cs = (k & 1) ? P->s_cmp : st;
-        PAMD_CUDA_TRY(cudaEventRecord(P->events[2 * k], P->s_in));
-        PAMD_CUDA_TRY(cudaStreamWaitEvent(cs, P->events[2 * k], 0));
+        const int lane = k % P->n_lanes;
+        cudaStream_t cs = lane ? P->s_cmp[lane - 1] : st;
+        PAMD_CUDA_TRY(cudaEventRecord(P->events[3 * k], P->s_in));
+        PAMD_CUDA_TRY(cudaStreamWaitEvent(cs, P->events[3 * k], 0));
         for (int u = 0; u < n_updates; ++u)
             if ((rc = run_one_update<R>(prob, P, (R*)dpos, (R*)dgrad, dS, nullptr, nullptr, dnacc, dla,
-                                        u, cs, c0, c1, P->d_chunk_counters + k, k & 1)))
+                                        u, cs, c0, c1, P->d_chunk_counters + k, lane)))
                 return rc;
-        PAMD_CUDA_TRY(cudaEventRecord(P->events[2 * k + 1], cs));
-        PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_out, P->events[2 * k + 1], 0));
+        PAMD_CUDA_TRY(cudaEventRecord(P->events[3 * k + 1], cs));
+        PAMD_CUDA_TRY(cudaStreamWaitEvent(P->s_out, P->events[3 * k + 1], 0));
         if (hp) PAMD_CUDA_TRY(cudaMemcpyAsync((char*)pos + off, dpos + off, nb, cudaMemcpyDeviceToHost, P->s_out));
         if (hg) PAMD_CUDA_TRY(cudaMemcpyAsync((char*)grad + off, dgrad + off, nb, cudaMemcpyDeviceToHost, P->s_out));
         if (hS)
@@ -815,10 +841,20 @@ int path_update_pipelined(const pamd_problem* prob, Plan* P, void* pos, void* gr
         if (hl)
             PAMD_CUDA_TRY(cudaMemcpyAsync(log_alpha + c0, dla + c0, sizeof(double) * (c1 - c0),
                                           cudaMemcpyDeviceToHost, P->s_out));
+        PAMD_CUDA_TRY(cudaEventRecord(P->events[3 * k + 2], P->s_out));
     }
     PAMD_CUDA_TRY(cudaEventRecord(ev_fin, P->s_out));
     PAMD_CUDA_TRY(cudaStreamWaitEvent(st, ev_fin, 0));
     PAMD_CUDA_TRY(cudaStreamSynchronize(st));
+    // timeline of this call
+    std::vector<float> tl(1 + 3 * K, 0.0f);
+    PAMD_CUDA_TRY(cudaEventElapsedTime(&tl[0], ev_start, ev_fin));
+    for (int k = 0; k < K; ++k) {
+        if (cut[k] >= cut[k + 1]) continue;
+        for (int q = 0; q < 3; ++q)
+            PAMD_CUDA_TRY(cudaEventElapsedTime(&tl[1 + 3 * k + q], ev_start, P->events[3 * k + q]));
+    }
+    g_last_timeline.swap(tl);
     return PAMD_OK;
 }
 
@@ -847,6 +883,16 @@ int pamd_release_cache(void)
     std::lock_guard<std::mutex> lk(g_mutex);
     cudaDeviceSynchronize();
     g_plans.clear();
+    return PAMD_OK;
+}
+
+int pamd_pipeline_timeline(float* ms, int max_entries, int* n_chunks)
+{
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (max_entries < 0 || (max_entries > 0 && !ms)) return PAMD_ERR_ARG;
+    const int n = (int)g_last_timeline.size();
+    if (n_chunks) *n_chunks = n ? (n - 1) / 3 : 0;
+    for (int q = 0; q < std::min(n, max_entries); ++q) ms[q] = g_last_timeline[q];
     return PAMD_OK;
 }
 
