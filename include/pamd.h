@@ -85,7 +85,29 @@ typedef struct {
 
 /* One system: n_chains independent paths of n_steps steps (n_steps+1 slices)
  * of n_particles particles in dim dimensions.  Supported: 1 <= dim <= 3,
- * n_steps >= 1; PAMD_LJ: 2 <= n_particles <= 1024. */
+ * n_steps >= 1; PAMD_LJ: 2 <= n_particles <= 1024.
+ *
+ * Time slabs.  The forces of different timesteps are independent (Sec. II.B),
+ * so one long path can be split in time over several processes: rank k of K
+ * owns steps [s_k, s_{k+1}) and slices [s_k, s_{k+1}) of every chain (the last
+ * rank also slice T).  Its buffer holds, per chain, the whole path's slices
+ * [s_k - halo_lo, s_{k+1}], so n_steps = s_{k+1} - s_k + halo_lo, and
+ *   first_slice : global index of local slice 0 (s_k - halo_lo);
+ *   halo_lo     : 1 when local slice 0 is the previous rank's last slice
+ *                 x_{s_k - 1}: its step only supplies the residual r_{s_k - 1}
+ *                 that the gradient at x_{s_k} needs (its force is evaluated
+ *                 here again, so ranks exchange positions only); 0 for rank 0
+ *                 (then first_slice = 0);
+ *   halo_hi     : 1 when the last local slice is the next rank's first slice
+ *                 x_{s_{k+1}} (its gradient belongs to that rank); 0 for the
+ *                 last rank.
+ * pamd_action and pamd_action_grad then return this rank's part of S (its
+ * owned steps; the caller sums the parts) and the whole path's gradient at the
+ * owned slices; the halo slices of grad are left unchanged.  The MALA pieces
+ * below work on the owned slices and draw the whole path's noise (elements
+ * counted from global slice 0).  Every other entry point requires
+ * first_slice = halo_lo = halo_hi = 0 (whole paths), PAMD_ERR_UNSUPPORTED
+ * otherwise. */
 typedef struct {
     int n_particles;
     int n_steps;
@@ -93,6 +115,8 @@ typedef struct {
     int n_chains;
     long long pos_offset;  /* element offset of chain 0, slice 0 in pos/grad buffers */
     pamd_potential pot;
+    long long first_slice; /* time slab: global index of local slice 0 (0: whole path) */
+    int halo_lo, halo_hi;  /* time slab: halo slice below / above the owned slices */
 } pamd_system;
 
 /* A batch of systems sharing D, beta, dt (paper notation; dt is the path
@@ -164,6 +188,48 @@ int pamd_action_grad(const pamd_problem* prob, const void* pos, double* S, void*
 int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S, double h,
                      int n_updates, uint64_t seed, uint64_t counter, const void* noise,
                      const double* log_u, int* n_accepted, double* log_alpha, void* stream);
+
+/* The update of pamd_path_update in pieces, for callers that split paths in
+ * time over several processes (time slabs, see pamd_system) and must sum each
+ * piece's per-chain terms over the processes before the next piece.  On whole
+ * paths the sequence
+ *     pamd_mala_propose -> pamd_action_grad(prop) -> pamd_mala_reverse
+ *     -> pamd_mala_accept -> pamd_mala_commit
+ * gives bitwise the result of pamd_path_update with n_updates = 1 and the same
+ * seed, counter, noise and log_u.  Device pointers only (PAMD_ERR_ARG
+ * otherwise); asynchronous on `stream`.
+ *
+ * pamd_mala_propose: prop = x - h g + sqrt(2h) eta on the owned slices other
+ *   than the fixed tail (global slice 0); the other slices of prop are copied
+ *   from pos.  q_fwd : double[n_chains_total], written, this slab's part of
+ *   sum |x' - x + h g|^2 over those slices.  noise: NULL (Philox stream 1, the
+ *   element index counted from global slice 0) or normals in the layout of pos. */
+int pamd_mala_propose(const pamd_problem* prob, const void* pos, const void* grad, void* prop,
+                      double h, uint64_t seed, uint64_t counter, const void* noise, double* q_fwd,
+                      void* stream);
+
+/* pamd_mala_reverse: q_rev : double[n_chains_total], written, this slab's part of
+ *   sum |x - x' + h g(x')|^2 over the proposed slices. */
+int pamd_mala_reverse(const pamd_problem* prob, const void* pos, const void* prop,
+                      const void* grad_prop, double h, double* q_rev, void* stream);
+
+/* pamd_mala_accept: per chain, from whole-path sums (device double[n_chains_total]
+ *   each: S = S(x), S_prop = S(x'), q_fwd, q_rev),
+ *       log alpha = S - S_prop - q_rev/(4h) + q_fwd/(4h),
+ *   accepted iff log u < log alpha, in double; log_u NULL (Philox stream 2,
+ *   counter) or double[n_chains_total].  accept : int[n_chains_total], written
+ *   (1 or 0); n_accepted (incremented) and log_alpha (written) may be NULL.  The
+ *   same inputs give the same decisions on every process. */
+int pamd_mala_accept(const pamd_problem* prob, const double* S, const double* S_prop,
+                     const double* q_fwd, const double* q_rev, double h, uint64_t seed,
+                     uint64_t counter, const double* log_u, int* accept, int* n_accepted,
+                     double* log_alpha, void* stream);
+
+/* pamd_mala_commit: for every chain with accept[c] != 0, pos <- prop and
+ *   grad <- grad_prop over all its slices (halos included) and S[c] <- S_prop[c]. */
+int pamd_mala_commit(const pamd_problem* prob, void* pos, void* grad, double* S, const void* prop,
+                     const void* grad_prop, const double* S_prop, const int* accept,
+                     void* stream);
 
 /* Forward Euler-Maruyama paths (Eq. (2)), sequential in time:
  *     x_{t+1} = x_t + beta D dt F(x_t) + sqrt(2 D dt) xi_t,
@@ -304,8 +370,8 @@ int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, doub
  * the library: PAMD_NOALLOC_MAX_BLOCKS doubles (512 KiB) of block sums, one
  * per 4096 elements of every chain.  Every GPU that loads the library holds
  * that array until the process exits.
- *   prob : harmonic systems only (PAMD_FP32 or PAMD_FP64); otherwise
- *          PAMD_ERR_ARG.  A problem needing more than PAMD_NOALLOC_MAX_BLOCKS
+ *   prob : harmonic systems only (PAMD_FP32 or PAMD_FP64), whole paths; otherwise
+ *          PAMD_ERR_ARG (time slabs: PAMD_ERR_UNSUPPORTED).  A problem needing more than PAMD_NOALLOC_MAX_BLOCKS
  *          blocks (sum over chains of ceil((T+1)*dim*N / 4096)), or with a
  *          system of more than 65535 chains, is rejected with
  *          PAMD_ERR_UNSUPPORTED before anything is enqueued.

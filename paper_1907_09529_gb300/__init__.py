@@ -21,7 +21,8 @@ from ._lib import (PAMD_FLAG_HO_EXACT_PROPAGATOR, PAMD_FLAG_ONE_CHAIN_PER_LAUNCH
                    PamdError, pamd_action, pamd_action_grad, pamd_device_status, pamd_euler_reference,
                    pamd_event, pamd_fragment_mc, pamd_shift_regenerate,
                    pamd_lj_pair_counts, pamd_normals, pamd_path_update, pamd_philox,
-                   pamd_cache_stats, pamd_release_cache, pamd_tune, pamd_version)
+                   pamd_cache_stats, pamd_mala_accept, pamd_mala_commit, pamd_mala_propose,
+                   pamd_mala_reverse, pamd_release_cache, pamd_tune, pamd_version)
 
 __all__ = [
     "System", "Problem", "action", "action_grad", "path_update", "euler_reference",
@@ -30,6 +31,8 @@ __all__ = [
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_release_cache", "pamd_tune",
     "pamd_version", "pamd_device_status", "device_status", "pamd_fragment_mc", "fragment_mc",
     "fragment_slots", "pamd_shift_regenerate", "pamd_event", "pamd_cache_stats", "cache_stats",
+    "mala_propose", "mala_reverse", "mala_accept", "mala_commit", "pamd_mala_propose",
+    "pamd_mala_reverse", "pamd_mala_accept", "pamd_mala_commit",
 ]
 
 ALIGN = 8  # system offsets are rounded to 8 elements (>= 16 bytes)
@@ -48,6 +51,11 @@ class System:
     rc: float = 2.5      # LJ cutoff (must be <= box/2)
     eps: float = 1.0
     sigma: float = 1.0
+    # time slab (see timeslab.py): whole-path index of local slice 0 and the halo
+    # slices below / above the owned ones; zeros for whole paths
+    first_slice: int = 0
+    halo_lo: int = 0
+    halo_hi: int = 0
 
     @property
     def chain_len(self) -> int:
@@ -86,7 +94,8 @@ class Problem:
         for q, s in enumerate(self.systems):
             kind = PAMD_HARMONIC if s.kind == "harmonic" else PAMD_LJ
             arr[q] = _lib.pamd_system(s.N, s.T, s.d, s.n_chains, self.offsets[q],
-                                      _lib.pamd_potential(kind, s.k, s.eps, s.sigma, s.rc, s.box))
+                                      _lib.pamd_potential(kind, s.k, s.eps, s.sigma, s.rc, s.box),
+                                      s.first_slice, s.halo_lo, s.halo_hi)
         self._systems_arr = arr
         flags = PAMD_FLAG_ONE_CHAIN_PER_LAUNCH if one_chain_per_launch else 0
         if ho_exact_propagator:
@@ -164,6 +173,52 @@ def path_update(p: Problem, pos: torch.Tensor, grad: torch.Tensor, S: torch.Tens
     pamd_path_update(p.ref, _ptr(pos), _ptr(grad), _ptr(S), float(h), int(n_updates),
                      int(seed), int(counter), _ptr(noise), _ptr(log_u), _ptr(n_accepted),
                      _ptr(log_alpha), _stream(pos, stream))
+
+
+def mala_propose(p: Problem, pos: torch.Tensor, grad: torch.Tensor, h: float, seed: int = 0,
+                 counter: int = 0, noise: Optional[torch.Tensor] = None,
+                 prop: Optional[torch.Tensor] = None, q_fwd: Optional[torch.Tensor] = None,
+                 stream=None):
+    """First piece of a path update (pamd_mala_propose): the proposal and this
+    slab's part of the forward proposal term, per chain."""
+    _check_buf(p, pos, "pos")
+    if prop is None:
+        prop = torch.empty_like(pos)
+    if q_fwd is None:
+        q_fwd = torch.empty(p.n_chains, dtype=torch.float64, device=pos.device)
+    pamd_mala_propose(p.ref, _ptr(pos), _ptr(grad), _ptr(prop), float(h), int(seed), int(counter),
+                      _ptr(noise), _ptr(q_fwd), _stream(pos, stream))
+    return prop, q_fwd
+
+
+def mala_reverse(p: Problem, pos: torch.Tensor, prop: torch.Tensor, grad_prop: torch.Tensor,
+                 h: float, q_rev: Optional[torch.Tensor] = None, stream=None):
+    """This slab's part of the reverse proposal term, per chain (pamd_mala_reverse)."""
+    if q_rev is None:
+        q_rev = torch.empty(p.n_chains, dtype=torch.float64, device=pos.device)
+    pamd_mala_reverse(p.ref, _ptr(pos), _ptr(prop), _ptr(grad_prop), float(h), _ptr(q_rev),
+                      _stream(pos, stream))
+    return q_rev
+
+
+def mala_accept(p: Problem, S: torch.Tensor, S_prop: torch.Tensor, q_fwd: torch.Tensor,
+                q_rev: torch.Tensor, h: float, seed: int = 0, counter: int = 0,
+                log_u: Optional[torch.Tensor] = None, n_accepted: Optional[torch.Tensor] = None,
+                log_alpha: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Metropolis-Hastings decisions from whole-path sums (pamd_mala_accept)."""
+    accept = torch.empty(p.n_chains, dtype=torch.int32, device=S.device)
+    pamd_mala_accept(p.ref, _ptr(S), _ptr(S_prop), _ptr(q_fwd), _ptr(q_rev), float(h), int(seed),
+                     int(counter), _ptr(log_u), _ptr(accept), _ptr(n_accepted), _ptr(log_alpha),
+                     _stream(S, stream))
+    return accept
+
+
+def mala_commit(p: Problem, pos: torch.Tensor, grad: torch.Tensor, S: torch.Tensor,
+                prop: torch.Tensor, grad_prop: torch.Tensor, S_prop: torch.Tensor,
+                accept: torch.Tensor, stream=None):
+    """Accepted chains take the proposal, its gradient and action (pamd_mala_commit)."""
+    pamd_mala_commit(p.ref, _ptr(pos), _ptr(grad), _ptr(S), _ptr(prop), _ptr(grad_prop),
+                     _ptr(S_prop), _ptr(accept), _stream(pos, stream))
 
 
 def euler_reference(p: Problem, pos: torch.Tensor, seed: int = 0, counter: int = 0,

@@ -36,6 +36,7 @@ EXPORTS = (
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
     "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate", "pamd_event",
     "pamd_cache_stats", "pamd_fp32_fma_probe", "pamd_pipeline_timeline",
+    "pamd_mala_propose", "pamd_mala_reverse", "pamd_mala_accept", "pamd_mala_commit",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -50,7 +51,8 @@ class pamd_potential(ctypes.Structure):
 class pamd_system(ctypes.Structure):
     _fields_ = [("n_particles", ctypes.c_int), ("n_steps", ctypes.c_int), ("dim", ctypes.c_int),
                 ("n_chains", ctypes.c_int), ("pos_offset", ctypes.c_longlong),
-                ("pot", pamd_potential)]
+                ("pot", pamd_potential), ("first_slice", ctypes.c_longlong),
+                ("halo_lo", ctypes.c_int), ("halo_hi", ctypes.c_int)]
 
 
 class pamd_problem(ctypes.Structure):
@@ -101,6 +103,12 @@ def load(path: str = LIB_PATH):
             "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
             "pamd_device_status": (ctypes.c_int, [_VP]),
             "pamd_cache_stats": (ctypes.c_int, [_VP, _VP]),
+            "pamd_mala_propose": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.c_double, u64, u64,
+                                                 _VP, _VP, _VP]),
+            "pamd_mala_reverse": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
+            "pamd_mala_accept": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP, ctypes.c_double, u64, u64,
+                                                _VP, _VP, _VP, _VP, _VP]),
+            "pamd_mala_commit": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
             "pamd_pipeline_timeline": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
             "pamd_fp32_fma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, _VP, _VP, _VP]),
@@ -144,6 +152,24 @@ def pamd_path_update(prob, pos, grad, S, h, n_updates, seed, counter, noise, log
                      log_alpha, stream):
     return _call("pamd_path_update", prob, pos, grad, S, h, n_updates, seed, counter, noise,
                  log_u, n_accepted, log_alpha, stream)
+
+
+def pamd_mala_propose(prob, pos, grad, prop, h, seed, counter, noise, q_fwd, stream):
+    return _call("pamd_mala_propose", prob, pos, grad, prop, h, seed, counter, noise, q_fwd, stream)
+
+
+def pamd_mala_reverse(prob, pos, prop, grad_prop, h, q_rev, stream):
+    return _call("pamd_mala_reverse", prob, pos, prop, grad_prop, h, q_rev, stream)
+
+
+def pamd_mala_accept(prob, S, S_prop, q_fwd, q_rev, h, seed, counter, log_u, accept, n_accepted,
+                     log_alpha, stream):
+    return _call("pamd_mala_accept", prob, S, S_prop, q_fwd, q_rev, h, seed, counter, log_u,
+                 accept, n_accepted, log_alpha, stream)
+
+
+def pamd_mala_commit(prob, pos, grad, S, prop, grad_prop, S_prop, accept, stream):
+    return _call("pamd_mala_commit", prob, pos, grad, S, prop, grad_prop, S_prop, accept, stream)
 
 
 def pamd_euler_reference(prob, pos, seed, counter, noise, stream):

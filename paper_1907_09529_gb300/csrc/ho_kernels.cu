@@ -8,7 +8,9 @@
 //   g_t = [r_{t-1} - r_t + a k r_t] / (2 D dt),   r_{-1} = r_T = 0.
 // Every coordinate is an independent time series; in the slice-major layout
 // pos[t][c][n] the time neighbours of element e are e - s and e + s, s = dim*N.
-// One pass reads each position once and writes each gradient once.
+// One pass reads each position once and writes each gradient once.  On a time
+// slab (see pamd_system) the halo step's residual is formed but not summed, and
+// the halo slices' gradients are not written (ElemBlock::sum_lo, own_lo/own_hi).
 #include "pamd_internal.cuh"
 
 namespace pamd {
@@ -45,8 +47,8 @@ __global__ void __launch_bounds__(kElemThreads)
         const R xm = xs[q], x0 = xs[q + s], xp = xs[q + 2 * s];
         const R rp = (e >= s) ? fma_r(ak, xm, x0 - xm) : R(0);
         const R r = (e < rend) ? fma_r(ak, x0, xp - x0) : R(0);
-        if (GRAD) grad[B.chain_base + e] = fma_r(ak, r, rp - r) * ginv;
-        acc = fma_r(r, r, acc);
+        if (GRAD && e >= B.own_lo && e < B.own_hi) grad[B.chain_base + e] = fma_r(ak, r, rp - r) * ginv;
+        if (e >= B.sum_lo) acc = fma_r(r, r, acc);
     }
     const double tot = block_sum((double)acc, red);
     if (threadIdx.x == 0) partials[slot0 + blockIdx.x] = tot;
@@ -115,10 +117,17 @@ __global__ void __launch_bounds__(kElemThreads)
             const float rp = (le >= S) ? fma_r(ak, xm, x0 - xm) : 0.f;
             const float r = (le < rend) ? fma_r(ak, x0, xp - x0) : 0.f;
             out[l] = fma_r(ak, r, rp - r) * ginv;
-            acc = fma_r(r, r, acc);
+            if (le >= B.sum_lo) acc = fma_r(r, r, acc);
         }
-        if (GRAD)
-            *reinterpret_cast<float4*>(grad + g) = make_float4(out[0], out[1], out[2], out[3]);
+        if (GRAD) {
+            if (le0 >= B.own_lo && le0 + 3 < B.own_hi) {
+                *reinterpret_cast<float4*>(grad + g) = make_float4(out[0], out[1], out[2], out[3]);
+            } else {  // a vector holding time-slab halo elements
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    if (le0 + l >= B.own_lo && le0 + l < B.own_hi) grad[g + l] = out[l];
+            }
+        }
     }
     // unaligned ends: [glo, gal) and [gah, ghi) (at most 3 + 3 elements), or the
     // whole block (fewer than 8 elements) when it holds no aligned float4
@@ -133,8 +142,8 @@ __global__ void __launch_bounds__(kElemThreads)
         const float xp = le < rend ? pos[g + S] : 0.f;
         const float rp = (le >= S) ? fma_r(ak, xm, x0 - xm) : 0.f;
         const float r = (le < rend) ? fma_r(ak, x0, xp - x0) : 0.f;
-        if (GRAD) grad[g] = fma_r(ak, r, rp - r) * ginv;
-        acc = fma_r(r, r, acc);
+        if (GRAD && le >= B.own_lo && le < B.own_hi) grad[g] = fma_r(ak, r, rp - r) * ginv;
+        if (le >= B.sum_lo) acc = fma_r(r, r, acc);
     }
     const double tot = block_sum((double)acc, red);
     if (threadIdx.x == 0) partials[slot0 + blockIdx.x] = tot;

@@ -315,7 +315,7 @@ __device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, u
         xb = tmp;
         if (pf) xb[threadIdx.x] = make4<R>(px, py, pz);
     }
-    if (GRAD && t1 == T && lead) {
+    if (GRAD && t1 == T && S.write_nose && lead) {
         R* Gt = G + (long long)T * s;
         Gt[i] = rpx * k.ginv;
         Gt[N + i] = rpy * k.ginv;

@@ -680,7 +680,7 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
         if (pf) store(threadIdx.x, nv);
         __syncthreads();
     }
-    if (GRAD && t1 == T && lead) {
+    if (GRAD && t1 == T && S.write_nose && lead) {
         float* Gt = G + (long long)T * s + i;
         Gt[0] = rpx * k.ginv;
         Gt[N] = rpy * k.ginv;
@@ -865,7 +865,7 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
         if (next) ensure_window(a + 2, min(a + (p + 2 < np ? 5 : 3), t1));
         __syncthreads();
     }
-    if (t1 == T && lead) {
+    if (t1 == T && S.write_nose && lead) {
         float* Gt = G + (long long)T * s + i;
         Gt[0] = rpx * k.ginv;
         Gt[N] = rpy * k.ginv;

@@ -164,6 +164,7 @@ extern "C" int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void*
             return PAMD_ERR_ARG;
         if (s.dim * s.n_particles > 8192) return PAMD_ERR_UNSUPPORTED;
         if (s.n_chains > 65535) return PAMD_ERR_UNSUPPORTED;  // one grid row per chain
+        if (s.first_slice || s.halo_lo || s.halo_hi) return PAMD_ERR_UNSUPPORTED;  // whole paths
         const long long chain_len = (long long)(s.n_steps + 1) * s.dim * s.n_particles;
         if (chain_len >= (1LL << 31)) return PAMD_ERR_UNSUPPORTED;
         blocks += (long long)s.n_chains * ((chain_len + pamd::kElemChunk - 1) / pamd::kElemChunk);

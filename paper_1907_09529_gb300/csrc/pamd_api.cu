@@ -8,6 +8,7 @@
 #include <cstring>
 #include <algorithm>
 #include <functional>
+#include <initializer_list>
 #include <type_traits>
 #include <map>
 #include <memory>
@@ -57,6 +58,8 @@ struct SysInfo {
     int ho_b0 = 0, ho_b1 = 0;  // harmonic: range of this system's element blocks
     int slot0 = 0;     // first S slot (LJ tiles)
     int n_tiles = 0;
+    long long first_slice = 0;   // time slab (0 / 0 / 0 for whole paths)
+    int halo_lo = 0, halo_hi = 0;
 };
 
 // Buffers and update count of a captured update graph.  Compared field by field:
@@ -177,6 +180,14 @@ int check_problem(const pamd_problem* p)
             return PAMD_ERR_ARG;
         const long long chain_len = (long long)(s.n_steps + 1) * s.dim * s.n_particles;
         if (chain_len >= (1LL << 31)) return PAMD_ERR_UNSUPPORTED;
+        // time slab: halo flags 0/1, a lower halo needs a slice before it, and at
+        // least one owned step
+        if (s.first_slice < 0 || (s.halo_lo != 0 && s.halo_lo != 1) ||
+            (s.halo_hi != 0 && s.halo_hi != 1) || (s.halo_lo && s.first_slice < 1) ||
+            s.n_steps - s.halo_lo < 1)
+            return PAMD_ERR_ARG;
+        if (s.first_slice + s.n_steps >= (1LL << 31) / std::max(1, s.dim * s.n_particles))
+            return PAMD_ERR_UNSUPPORTED;
         if (s.pot.kind == PAMD_HARMONIC) {
             if (s.dim * s.n_particles > 8192) return PAMD_ERR_UNSUPPORTED;
         } else if (s.pot.kind == PAMD_LJ) {
@@ -188,6 +199,16 @@ int check_problem(const pamd_problem* p)
         } else {
             return PAMD_ERR_ARG;
         }
+    }
+    return PAMD_OK;
+}
+
+// Entry points that need whole paths (no time slab).
+int check_whole_paths(const pamd_problem* p)
+{
+    for (int q = 0; q < p->n_systems; ++q) {
+        const pamd_system& s = p->systems[q];
+        if (s.first_slice || s.halo_lo || s.halo_hi) return PAMD_ERR_UNSUPPORTED;
     }
     return PAMD_OK;
 }
@@ -234,7 +255,8 @@ std::string plan_key(const pamd_problem* p)
         const pamd_system& s = p->systems[q];
         os << '|' << s.n_particles << ',' << s.n_steps << ',' << s.dim << ',' << s.n_chains << ','
            << s.pos_offset << ',' << s.pot.kind << ',' << s.pot.k << ',' << s.pot.eps << ','
-           << s.pot.sigma << ',' << s.pot.rc << ',' << s.pot.box;
+           << s.pot.sigma << ',' << s.pot.rc << ',' << s.pot.box << ',' << s.first_slice << ','
+           << s.halo_lo << ',' << s.halo_hi;
     }
     return os.str();
 }
@@ -330,6 +352,7 @@ void fill_lj_sys(Plan* P, const pamd_problem* p)
         // (PAMD_LJ_PER_STEP_SHIFT=1 rounds the image shift at every slice instead; the
         // results are bitwise the same, which a test checks)
         d.shared_shift = std::getenv("PAMD_LJ_PER_STEP_SHIFT") == nullptr;
+        d.write_nose = !si.halo_hi;
         LJConst c;
         c.L = si.pot.box;
         c.rc = si.pot.rc;
@@ -385,6 +408,9 @@ int build_plan(const pamd_problem* p, Plan** out)
         si.off = s.pos_offset;
         si.chain_len = (long long)(s.n_steps + 1) * s.dim * s.n_particles;
         si.pot = s.pot;
+        si.first_slice = s.first_slice;
+        si.halo_lo = s.halo_lo;
+        si.halo_hi = s.halo_hi;
         P->span = std::max(P->span, si.off + si.chain_len * si.chains);
         P->sys.push_back(si);
         chain += s.n_chains;
@@ -415,6 +441,10 @@ int build_plan(const pamd_problem* p, Plan** out)
                 B.chain = c;
                 B.sys = (int)(&si - &P->sys[0]);
                 B.k = si.pot.k;
+                B.e_glob = si.first_slice * s;
+                B.own_lo = si.halo_lo * s;
+                B.own_hi = (int)si.chain_len - si.halo_hi * s;
+                B.sum_lo = si.halo_lo * s;
                 P->h_all.push_back(B);
                 if (si.kind == PAMD_HARMONIC) P->h_ho.push_back(B);
             }
@@ -488,11 +518,12 @@ int build_plan(const pamd_problem* p, Plan** out)
                 for (auto& si : P->sys) {
                     if (si.kind != PAMD_LJ) continue;
                     const long long G = (long long)bg * sms;
-                    const long long items0 = (long long)si.chains * ((si.T + si.tune.tile_steps - 1) / si.tune.tile_steps);
+                    const int Tow = si.T - si.halo_lo;  // owned steps
+                    const long long items0 = (long long)si.chains * ((Tow + si.tune.tile_steps - 1) / si.tune.tile_steps);
                     const long long rounds = (items0 + G - 1) / G;
                     const long long per_chain = (rounds * G) / si.chains;
                     if (per_chain >= 1) {
-                        const int tile = (int)((si.T + per_chain - 1) / per_chain);
+                        const int tile = (int)((Tow + per_chain - 1) / per_chain);
                         if (tile >= std::min(16, si.tune.tile_steps)) si.tune.tile_steps = tile;
                     }
                 }
@@ -500,7 +531,7 @@ int build_plan(const pamd_problem* p, Plan** out)
             for (int q = 0; q < (int)P->sys.size(); ++q) {
                 SysInfo& si = P->sys[q];
                 if (si.kind != PAMD_LJ) continue;
-                si.n_tiles = (si.T + si.tune.tile_steps - 1) / si.tune.tile_steps;
+                si.n_tiles = (si.T - si.halo_lo + si.tune.tile_steps - 1) / si.tune.tile_steps;
                 si.slot0 = slot;
                 for (int b = 0; b < si.chains; ++b) {
                     const int c = si.chain0 + b;
@@ -512,7 +543,7 @@ int build_plan(const pamd_problem* p, Plan** out)
                         LJItem it;
                         it.sys = si.lj_index;
                         it.chain = b;
-                        it.t0 = tl * si.tune.tile_steps;
+                        it.t0 = si.halo_lo + tl * si.tune.tile_steps;  // owned steps only
                         it.t1 = std::min(si.T, it.t0 + si.tune.tile_steps);
                         it.slot = slot + b * si.n_tiles + tl;
                         items.push_back(it);
@@ -623,7 +654,7 @@ int ensure_update_ws(Plan* P)
     if ((rc = P->alloc(&P->d_qf, sizeof(double) * P->n_chains))) return rc;
     if ((rc = P->alloc(&P->d_qr, sizeof(double) * P->n_chains))) return rc;
     if ((rc = P->alloc(&P->d_flag, sizeof(int) * P->n_chains))) return rc;
-    if ((rc = P->alloc(&P->d_md, sizeof(MalaDev)))) return rc;
+    if (!P->d_md && (rc = P->alloc(&P->d_md, sizeof(MalaDev)))) return rc;
     PAMD_CUDA_TRY(cudaMemset(P->d_prop, 0, P->esz * (size_t)P->span));
     PAMD_CUDA_TRY(cudaMemset(P->d_gprop, 0, P->esz * (size_t)P->span));
     return PAMD_OK;
@@ -999,6 +1030,7 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
     NvtxRange nvtx_("pamd_path_update");
     int rc = check_em_problem(prob);
     if (rc) return rc;
+    if ((rc = check_whole_paths(prob))) return rc;
     if (!pos || !grad || !S || !(h > 0) || n_updates < 0) return PAMD_ERR_ARG;
     if ((noise || log_u) && n_updates != 1) return PAMD_ERR_ARG;
     if (n_updates == 0) return PAMD_OK;
@@ -1114,12 +1146,115 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
     return PAMD_OK;
 }
 
+// ------------------------------------------------------------------ update in pieces
+// The kernels of run_one_update, one piece per call, on the caller's buffers.
+static int mala_piece_plan(const pamd_problem* prob, std::initializer_list<const void*> bufs,
+                           Plan** P)
+{
+    int rc = check_em_problem(prob);
+    if (rc) return rc;
+    for (const void* b : bufs)
+        if (!b || is_host_ptr(b)) return PAMD_ERR_ARG;  // device buffers only
+    if ((rc = build_plan(prob, P))) return rc;
+    if (!(*P)->d_md && (rc = (*P)->alloc(&(*P)->d_md, sizeof(MalaDev)))) return rc;
+    return PAMD_OK;
+}
+
+int pamd_mala_propose(const pamd_problem* prob, const void* pos, const void* grad, void* prop,
+                      double h, uint64_t seed, uint64_t counter, const void* noise, double* q_fwd,
+                      void* stream)
+{
+    NvtxRange nvtx_("pamd_mala_propose");
+    if (!(h > 0) || (noise && is_host_ptr(noise))) return PAMD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    int rc = mala_piece_plan(prob, {pos, grad, prop, q_fwd}, &P);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = (int)P->h_all.size();
+    PAMD_CUDA_TRY(launch_set_mala_params(P->d_md, seed, counter, h, st));
+    if (P->fp64)
+        PAMD_CUDA_TRY(launch_mala_propose<double>(P->d_all, nb, (const double*)pos, (const double*)grad,
+                                                  (const double*)noise, (double*)prop, P->d_part_qf,
+                                                  P->d_md, 0, st));
+    else
+        PAMD_CUDA_TRY(launch_mala_propose<float>(P->d_all, nb, (const float*)pos, (const float*)grad,
+                                                 (const float*)noise, (float*)prop, P->d_part_qf,
+                                                 P->d_md, 0, st));
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_qf, P->d_E_slots, P->n_chains, 1.0, q_fwd, st));
+    return PAMD_OK;
+}
+
+int pamd_mala_reverse(const pamd_problem* prob, const void* pos, const void* prop,
+                      const void* grad_prop, double h, double* q_rev, void* stream)
+{
+    NvtxRange nvtx_("pamd_mala_reverse");
+    if (!(h > 0)) return PAMD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    int rc = mala_piece_plan(prob, {pos, prop, grad_prop, q_rev}, &P);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = (int)P->h_all.size();
+    PAMD_CUDA_TRY(launch_set_mala_params(P->d_md, 0, 0, h, st));
+    if (P->fp64)
+        PAMD_CUDA_TRY(launch_mala_reverse<double>(P->d_all, nb, (const double*)pos, (const double*)prop,
+                                                  (const double*)grad_prop, P->d_part_qr, P->d_md, st));
+    else
+        PAMD_CUDA_TRY(launch_mala_reverse<float>(P->d_all, nb, (const float*)pos, (const float*)prop,
+                                                 (const float*)grad_prop, P->d_part_qr, P->d_md, st));
+    PAMD_CUDA_TRY(launch_finalize(P->d_part_qr, P->d_E_slots, P->n_chains, 1.0, q_rev, st));
+    return PAMD_OK;
+}
+
+int pamd_mala_accept(const pamd_problem* prob, const double* S, const double* S_prop,
+                     const double* q_fwd, const double* q_rev, double h, uint64_t seed,
+                     uint64_t counter, const double* log_u, int* accept, int* n_accepted,
+                     double* log_alpha, void* stream)
+{
+    NvtxRange nvtx_("pamd_mala_accept");
+    if (!(h > 0)) return PAMD_ERR_ARG;
+    for (const void* b : {(const void*)log_u, (const void*)n_accepted, (const void*)log_alpha})
+        if (b && is_host_ptr(b)) return PAMD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    int rc = mala_piece_plan(prob, {S, S_prop, q_fwd, q_rev, accept}, &P);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    PAMD_CUDA_TRY(launch_set_mala_params(P->d_md, seed, counter, h, st));
+    PAMD_CUDA_TRY(launch_mala_accept(0, P->n_chains, S, S_prop, q_fwd, q_rev, log_u, P->d_md, 0,
+                                     accept, n_accepted, log_alpha, st));
+    return PAMD_OK;
+}
+
+int pamd_mala_commit(const pamd_problem* prob, void* pos, void* grad, double* S, const void* prop,
+                     const void* grad_prop, const double* S_prop, const int* accept, void* stream)
+{
+    NvtxRange nvtx_("pamd_mala_commit");
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    int rc = mala_piece_plan(prob, {pos, grad, S, prop, grad_prop, S_prop, accept}, &P);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = (int)P->h_all.size();
+    if (P->fp64)
+        PAMD_CUDA_TRY(launch_mala_commit<double>(P->d_all, nb, (double*)pos, (double*)grad,
+                                                 (const double*)prop, (const double*)grad_prop,
+                                                 accept, S, S_prop, st));
+    else
+        PAMD_CUDA_TRY(launch_mala_commit<float>(P->d_all, nb, (float*)pos, (float*)grad,
+                                                (const float*)prop, (const float*)grad_prop, accept,
+                                                S, S_prop, st));
+    return PAMD_OK;
+}
+
 int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uint64_t counter,
                          const void* noise, void* stream)
 {
     NvtxRange nvtx_("pamd_euler_reference");
     int rc = check_em_problem(prob);
     if (rc) return rc;
+    if ((rc = check_whole_paths(prob))) return rc;
     if (!pos) return PAMD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mutex);
     Plan* P;
@@ -1180,6 +1315,7 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
     NvtxRange nvtx_("pamd_fragment_mc");
     int rc = check_problem(prob);
     if (rc) return rc;
+    if ((rc = check_whole_paths(prob))) return rc;
     if (!pos || !n_accepted || !n_proposed || n_steps < 0 || l_min < 1 || l_max < l_min || l_max > 30)
         return PAMD_ERR_ARG;
     if ((levels || offsets || noise || log_u) && n_steps != 1) return PAMD_ERR_ARG;
@@ -1229,6 +1365,7 @@ int pamd_event(const pamd_problem* prob, void* pos, void* pos_out, int n_sample,
     NvtxRange nvtx_("pamd_event");
     int rc = check_problem(prob);
     if (rc) return rc;
+    if ((rc = check_whole_paths(prob))) return rc;
     if (!pos || !pos_out || !traj || pos == pos_out || !n_accepted || !n_proposed || n_sample < 1 ||
         n_shift < 1 || l_min < 1 || l_max < l_min || l_max > 30)
         return PAMD_ERR_ARG;
@@ -1294,6 +1431,7 @@ int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_o
     NvtxRange nvtx_("pamd_shift_regenerate");
     int rc = check_problem(prob);
     if (rc) return rc;
+    if ((rc = check_whole_paths(prob))) return rc;
     if (!pos || !pos_out || !traj || pos == pos_out || n_shift < 1) return PAMD_ERR_ARG;
     for (int q = 0; q < prob->n_systems; ++q)
         if (n_shift > prob->systems[q].n_steps) return PAMD_ERR_ARG;
@@ -1325,6 +1463,7 @@ int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* co
     NvtxRange nvtx_("pamd_lj_pair_counts");
     int rc = check_problem(prob);
     if (rc) return rc;
+    if ((rc = check_whole_paths(prob))) return rc;
     if (!pos || !counts || prob->precision != PAMD_FP32) return PAMD_ERR_ARG;
     if (is_host_ptr(pos) || is_host_ptr(counts)) return PAMD_ERR_ARG;
     for (int q = 0; q < prob->n_systems; ++q)  // one grid row per chain

@@ -149,12 +149,15 @@ __device__ __forceinline__ double block_sum(double v, double* scratch)
 // A contiguous run of elements of one chain (element-wise passes).
 struct ElemBlock {
     long long chain_base;  // element offset of the chain's slice 0 in the buffer
+    long long e_glob;      // whole-path index of chain-local element 0 (time slabs; else 0)
     int e0;                // first chain-local element handled by this block
     int n;                 // number of elements
     int s;                 // elements per slice (dim * N)
     int chain_len;         // (T+1) * s
     int chain;             // global chain index
     int sys;               // system index
+    int own_lo, own_hi;    // owned chain-local elements (gradient written, proposed)
+    int sum_lo;            // first element whose step counts in S (halo step excluded)
     double k;              // harmonic constant (harmonic systems)
 };
 
@@ -251,6 +254,7 @@ struct LJSysDev {
     int window;           // steps per neighbour-list window (paired kernel)
     int outer_cap;        // outer-list capacity per thread (paired kernel, global memory)
     int shared_shift;     // paired kernel: windows may use one image shift per list entry
+    int write_nose;       // the last slice is owned (not a time-slab halo): write its gradient
     LJK<R> k;
 };
 

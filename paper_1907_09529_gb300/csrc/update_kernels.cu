@@ -58,8 +58,10 @@ cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter,
     return cudaGetLastError();
 }
 
-// Each thread owns groups of 4 consecutive chain-local elements (one Philox
-// call gives the 4 normals of a group).
+// Each thread owns groups of 4 consecutive chain-local elements.  The normal of
+// element e is component (g & 3) of the Philox call for group g >> 2, g = e_glob + e
+// its whole-path index (one call per group on whole paths).  Elements outside
+// [s, own_hi) -- the fixed tail x_0 or a time slab's halo slices -- are copied.
 template <typename R>
 __global__ void __launch_bounds__(kElemThreads)
     mala_propose_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
@@ -73,22 +75,26 @@ __global__ void __launch_bounds__(kElemThreads)
     const uint64_t seed = md->seed, counter = md->counter + (uint64_t)update_index;
     const long long base = B.chain_base;
     R acc = R(0);
-    const int g0 = B.e0 >> 2;                 // e0 is a multiple of 4
-    const int ng = (B.n + 3) >> 2;
+    const int ng = (B.n + 3) >> 2;             // e0 is a multiple of 4
     for (int gq = threadIdx.x; gq < ng; gq += kElemThreads) {
         float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!noise) z4 = philox_normals4(seed, counter, kStreamMala, (uint32_t)B.chain, (uint32_t)(g0 + gq));
+        long long zg = -1;                     // Philox group held in z4
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             const int e = B.e0 + 4 * gq + l;
             if (e >= B.e0 + B.n) break;
             const R x = pos[base + e];
-            if (e < B.s) {  // tail slice x_0 is held fixed
+            if (e < B.s || e >= B.own_hi) {  // fixed tail x_0, or a time-slab halo
                 prop[base + e] = x;
                 continue;
             }
             const R g = grad[base + e];
-            const R z = noise ? noise[base + e] : (R)pick4(z4, l);
+            const long long ge = B.e_glob + e;
+            if (!noise && (ge >> 2) != zg) {
+                zg = ge >> 2;
+                z4 = philox_normals4(seed, counter, kStreamMala, (uint32_t)B.chain, (uint32_t)zg);
+            }
+            const R z = noise ? noise[base + e] : (R)pick4(z4, (int)(ge & 3));
             const R xp = x + fma_r(-h, g, s2h * z);
             prop[base + e] = xp;
             const R f = fma_r(h, g, xp - x);
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(kElemThreads)
 #pragma unroll 4
     for (int q = threadIdx.x; q < B.n; q += kElemThreads) {
         const int e = B.e0 + q;
-        if (e < B.s) continue;
+        if (e < B.s || e >= B.own_hi) continue;
         const R x = pos[base + e], xp = prop[base + e], gp = grad_prop[base + e];
         const R b = fma_r(h, gp, x - xp);
         acc = fma_r(b, b, acc);
