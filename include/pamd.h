@@ -45,6 +45,14 @@
  * First use.  The first call for a given problem shape builds a plan and
  * allocates its device workspace (cudaMalloc); make that first call before
  * any stream capture.  pamd_release_cache() frees all of it.
+ *
+ * Fault injection (tests of the error paths; nothing faults on the device).
+ * With the environment variable PAMD_FAULT_INJECT set to "alloc", every
+ * workspace allocation fails (PAMD_ERR_ALLOC; a plan that could not be built is
+ * not cached); "launch": every CUDA call the library checks reports failure
+ * (PAMD_ERR_CUDA; a graph whose capture failed is not cached); "nonfinite":
+ * every action computed is flagged non-finite (pamd_device_status then returns
+ * PAMD_ERR_NONFINITE).  The variable is read at each call.
  */
 #ifndef PAMD_H
 #define PAMD_H

@@ -32,10 +32,20 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
-#define PAMD_CUDA_TRY(expr)                           \
-    do {                                              \
-        cudaError_t _e = (expr);                      \
-        if (_e != cudaSuccess) return PAMD_ERR_CUDA;  \
+// Host-side fault injection, for tests of the error paths (nothing faults on the
+// device): PAMD_FAULT_INJECT=alloc makes every workspace allocation fail,
+// =launch makes every CUDA call the library checks report failure, =nonfinite
+// flags every action computed as non-finite.
+bool fault_injected(const char* what)
+{
+    const char* e = std::getenv("PAMD_FAULT_INJECT");
+    return e && std::strcmp(e, what) == 0;
+}
+
+#define PAMD_CUDA_TRY(expr)                                                    \
+    do {                                                                       \
+        cudaError_t _e = (expr);                                               \
+        if (_e != cudaSuccess || fault_injected("launch")) return PAMD_ERR_CUDA; \
     } while (0)
 
 struct LJTune {
@@ -156,7 +166,7 @@ struct Plan {
     {
         void* q = nullptr;
         if (bytes == 0) bytes = 16;
-        if (cudaMalloc(&q, bytes) != cudaSuccess) return PAMD_ERR_ALLOC;
+        if (fault_injected("alloc") || cudaMalloc(&q, bytes) != cudaSuccess) return PAMD_ERR_ALLOC;
         allocs.push_back(q);
         *p = reinterpret_cast<T*>(q);
         return PAMD_OK;
@@ -739,6 +749,7 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
     }
     PAMD_CUDA_TRY(launch_finalize(P->d_part_S, P->d_S_slots + c0, c1 - c0, 1.0 / (4.0 * p->D * p->dt),
                                   S_out + c0, st, P->d_err));
+    if (fault_injected("nonfinite")) PAMD_CUDA_TRY(launch_set_status(P->d_err, PAMD_ERR_NONFINITE, st));
     return PAMD_OK;
 }
 

@@ -307,6 +307,9 @@ cudaError_t launch_lj_euler(R* pos, const R* noise, const void* sys_entry_host, 
 cudaError_t launch_finalize(const double* partials, const ChainSlots* slots, int n_chains,
                             double scale, double* out, cudaStream_t st, int* err = nullptr);
 
+// Sets a device status word (host-side fault injection of non-finite actions).
+cudaError_t launch_set_status(int* err, int v, cudaStream_t st);
+
 // MALA update pieces (element-wise over all systems' blocks).
 struct MalaDev {
     uint64_t seed;

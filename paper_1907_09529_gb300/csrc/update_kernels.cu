@@ -43,6 +43,14 @@ cudaError_t launch_finalize(const double* partials, const ChainSlots* slots, int
     return cudaGetLastError();
 }
 
+__global__ void set_status_kernel(int* err, int v) { *err = v; }
+
+cudaError_t launch_set_status(int* err, int v, cudaStream_t st)
+{
+    set_status_kernel<<<1, 1, 0, st>>>(err, v);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ MALA pieces
 __global__ void set_mala_params_kernel(MalaDev* md, uint64_t seed, uint64_t counter, double h)
 {
