@@ -414,6 +414,20 @@ int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void* pos, doubl
 int pamd_fp32_fma_probe(int packed, int blocks, int threads, int iters, float* out,
                         double* flops, void* stream);
 
+/* Bounds checks of the debug build (a diagnostic; the paper has no counterpart).
+ * libpamd_debug.so is this library compiled with -DPAMD_DEBUG: every array
+ * index of the Lennard-Jones, oscillator, update and multilevel-sampler kernels
+ * is checked, and an index outside its array is recorded on the device and the
+ * access sent to a scratch sink instead (nothing traps, nothing outside the
+ * arrays is touched).  This call synchronises the device, then reports
+ *   *checked : 1 in the debug build, 0 in the normal library (no checks);
+ *   *count   : out-of-bounds accesses recorded since the last call;
+ *   *site, *index, *bound : the first of them: file * 100000 + source line
+ *              (files 1..5: ho_kernels, lj_kernels, lj_paired, update_kernels,
+ *              fragment_kernels), the index and the array's extent,
+ * and clears the records.  Any pointer may be NULL. */
+int pamd_debug_status(int* checked, int* count, int* site, long long* index, long long* bound);
+
 /* Human-readable name of a status code (static string). */
 const char* pamd_status_string(int status);
 

@@ -11,7 +11,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpamd.so")
+# PAMD_LIBRARY=debug loads the bounds-checked build (libpamd_debug.so) instead
+LIB_PATH = os.path.join(HERE, "libpamd_debug.so" if os.environ.get("PAMD_LIBRARY") == "debug"
+                        else "libpamd.so")
 
 PAMD_OK = 0
 PAMD_ERR_ARG = -1
@@ -37,6 +39,7 @@ EXPORTS = (
     "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate", "pamd_event",
     "pamd_cache_stats", "pamd_fp32_fma_probe", "pamd_pipeline_timeline",
     "pamd_mala_propose", "pamd_mala_reverse", "pamd_mala_accept", "pamd_mala_commit",
+    "pamd_debug_status",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -103,6 +106,7 @@ def load(path: str = LIB_PATH):
             "pamd_ho_action_grad_noalloc": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP]),
             "pamd_device_status": (ctypes.c_int, [_VP]),
             "pamd_cache_stats": (ctypes.c_int, [_VP, _VP]),
+            "pamd_debug_status": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
             "pamd_mala_propose": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.c_double, u64, u64,
                                                  _VP, _VP, _VP]),
             "pamd_mala_reverse": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
@@ -225,6 +229,15 @@ def pamd_pipeline_timeline():
     buf = (ctypes.c_float * (1 + 3 * n.value))()
     _call("pamd_pipeline_timeline", buf, 1 + 3 * n.value, ctypes.byref(n))
     return buf[0], [tuple(buf[1 + 3 * k:4 + 3 * k]) for k in range(n.value)]
+
+
+def pamd_debug_status():
+    """(checks compiled, out-of-bounds accesses, first site, its index, its bound)
+    of the kernels since the last call; see include/pamd.h."""
+    v = [ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_longlong(0),
+         ctypes.c_longlong(0)]
+    _call("pamd_debug_status", *[ctypes.byref(x) for x in v])
+    return tuple(x.value for x in v)
 
 
 def pamd_cache_stats():

@@ -182,28 +182,28 @@ __global__ void __launch_bounds__(kFragMaxThreads)
 
     auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     unsigned char* p = frag_smem;
-    R* FS = (R*)p;
-    R* FS0 = FS + nfrag_max;
+    PAMD_ARR(R, FS, (R*)p, nfrag_max);
+    PAMD_ARR(R, FS0, (R*)p + nfrag_max, nfrag_max);
     p += up16(2 * sizeof(R) * nfrag_max);
-    R* X = (R*)p;
+    PAMD_ARR(R, X, (R*)p, E);
     p += up16(sizeof(R) * (size_t)E);
-    R* W = (R*)p;
+    PAMD_ARR(R, W, (R*)p, E);
     p += up16(sizeof(R) * (size_t)E);
-    R* WB = (R*)p;
+    PAMD_ARR(R, WB, (R*)p, (long long)nfrag_max * M);
     p += up16(sizeof(R) * (size_t)nfrag_max * M);
-    R* tail = (R*)p;
-    R* tS = tail + NW * M;
-    R* tS0 = tS + NW;
+    PAMD_ARR(R, tail, (R*)p, NW * M);
+    PAMD_ARR(R, tS, (R*)p + NW * M, NW);
+    PAMD_ARR(R, tS0, (R*)p + NW * M + NW, NW);
     p += up16(sizeof(R) * (size_t)NW * (M + 2));
-    int* accf = (int*)p;
-    int* cnt = accf + nfrag_max;
+    PAMD_ARR(int, accf, (int*)p, nfrag_max);
+    PAMD_ARR(int, cnt, (int*)p + nfrag_max, 2);
 
-    R* gX = pos + S.off + (long long)b_chain * E;
+    PAMD_ARR(R, gX, pos + S.off + (long long)b_chain * E, E);
     // 1. stage the path, draw sig z into W (slices 1..T), clear the sums
 #pragma unroll 4
     for (int e = tid; e < E; e += nt) X[e] = gX[e];
     if (noise) {
-        const R* gZ = noise + S.off + (long long)b_chain * E;
+        PAMD_ARR(const R, gZ, noise + S.off + (long long)b_chain * E, E);
 #pragma unroll 4
         for (int e = M + tid; e < E; e += nt) W[e] = sig * gZ[e];
     } else {
@@ -539,31 +539,32 @@ __global__ void __launch_bounds__(kFragMaxThreads)
 
     auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     unsigned char* p = frag_smem;
-    R* FS = (R*)p;
-    R* FS0 = FS + nfrag_max;
+    PAMD_ARR(R, FS, (R*)p, nfrag_max);
+    PAMD_ARR(R, FS0, (R*)p + nfrag_max, nfrag_max);
     p += up16(2 * sizeof(R) * nfrag_max);
-    R* X = (R*)p;
+    PAMD_ARR(R, X, (R*)p, Q * 4);
     p += up16(sizeof(R) * (size_t)Q * 4);
-    R* W = (R*)p;
+    PAMD_ARR(R, W, (R*)p, Q * 4);
     p += up16(sizeof(R) * (size_t)Q * 4);
-    R* WB = (R*)p;
+    PAMD_ARR(R, WB, (R*)p, nfrag_max);
     p += up16(sizeof(R) * (size_t)nfrag_max);
-    R* tW = (R*)p;
-    R* tS = tW + NW;
-    R* tS0 = tS + NW;
+    PAMD_ARR(R, tW, (R*)p, NW);
+    PAMD_ARR(R, tS, (R*)p + NW, NW);
+    PAMD_ARR(R, tS0, (R*)p + 2 * NW, NW);
     p += up16(sizeof(R) * (size_t)NW * 3);
-    R* Zs = (R*)p;
+    PAMD_ARR(R, Zs, (R*)p, sh.out ? sh.n_shift : 0);
     p += up16(sizeof(R) * (size_t)(sh.out ? sh.n_shift : 0));
-    int* accf = (int*)p;
-    int* aflag = accf + nfrag_max;
-    int* cnt = aflag + nfrag_max;
+    PAMD_ARR(int, accf, (int*)p, nfrag_max);
+    PAMD_ARR(int, aflag, (int*)p + nfrag_max, nfrag_max);
+    PAMD_ARR(int, cnt, (int*)p + 2 * nfrag_max, 2);
 
-    R* gX = pos + S.off + (long long)b_chain * E;
-    const R* gZ = noise ? noise + S.off + (long long)b_chain * E : nullptr;
+    PAMD_ARR(R, gX, pos + S.off + (long long)b_chain * E, E);
+    PAMD_ARR(const R, gZ, noise ? noise + S.off + (long long)b_chain * E : nullptr, E);
     // 1. stage the path asynchronously (quads padded with zeros); it is first
     //    read in step 4
 #pragma unroll 4
-    for (int e = tid; e < E; e += nt) cp_async_elem(X + e, gX + e);
+    for (int e = tid; e < E; e += nt)
+        if (PAMD_OK_IDX(e, Q * 4)) cp_async_elem((R*)X + e, (R*)gX + e);
     cp_async_commit();
     if (tid < Q * 4 - E) X[E + tid] = R(0);
     if (tid == 0) cnt[0] = cnt[1] = 0;
@@ -611,7 +612,7 @@ __global__ void __launch_bounds__(kFragMaxThreads)
                 k[j] = G.of_step(min(max(e, 1), T));
             }
             quad_scan<R, 1>(v, k, lane, carry, ckey, min(31, q_hi - 1 - q0));
-            if (qa) store_quad(W + 4 * q, v[0]);
+            if (qa && PAMD_OK_IDX(4 * q + 3, Q * 4)) store_quad((R*)W + 4 * q, v[0]);
         }
         if (lane == 0) tW[warp] = (q_lo < q_hi) ? carry[0] : R(0);
     }
@@ -664,8 +665,9 @@ __global__ void __launch_bounds__(kFragMaxThreads)
             R v[2][4];
             int k[4];
             R y[4];
-            const Quad<R> xq = load_quad(X + 4 * min(q, Q - 1));
-            const Quad<R> wq = load_quad(W + 4 * min(q, Q - 1));
+            const bool qok = PAMD_OK_IDX(4 * min(q, Q - 1) + 3, Q * 4);
+            const Quad<R> xq = load_quad((R*)X + 4 * (qok ? min(q, Q - 1) : 0));
+            const Quad<R> wq = load_quad((R*)W + 4 * (qok ? min(q, Q - 1) : 0));
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int ec = min(max(4 * q + j, 1), T);
@@ -760,8 +762,8 @@ __global__ void __launch_bounds__(kFragMaxThreads)
     // 6'. final path P: accepted interiors to the path, P shifted to `out`,
     //     P[1..n_shift] to the trajectory, and the nose regrown
     const int ns = sh.n_shift;
-    R* gO = sh.out + S.off + (long long)b_chain * E;
-    R* gT = sh.traj + (long long)b_chain * ns;
+    PAMD_ARR(R, gO, sh.out + S.off + (long long)b_chain * E, E);
+    PAMD_ARR(R, gT, sh.traj + (long long)b_chain * ns, ns);
     auto final_at = [&](int e) -> R {
         const int f = G.of_step(e);
         if (aflag[f] && (e < G.b(f) || f == G.nfrag - 1)) return trial(e, f, W[e]);
@@ -806,8 +808,9 @@ __global__ void __launch_bounds__(128)
     const int T = S.T, M = S.M, fa = G.a(f), fb = G.b(f);
     const bool nose = (f == G.nfrag - 1);
     if (!nose && fb - fa < 2) return;  // no interior point
-    R* X = pos + S.off + (long long)b_chain * (long long)(T + 1) * M;
-    const R* Z = noise ? noise + S.off + (long long)b_chain * (long long)(T + 1) * M : nullptr;
+    PAMD_ARR(R, X, pos + S.off + (long long)b_chain * (long long)(T + 1) * M, (long long)(T + 1) * M);
+    PAMD_ARR(const R, Z, noise ? noise + S.off + (long long)b_chain * (long long)(T + 1) * M : nullptr,
+             (long long)(T + 1) * M);
 
     auto znorm = [&](int t, int m) -> R {
         const long long e = (long long)t * M + m;
@@ -1038,5 +1041,7 @@ template cudaError_t launch_shift_regenerate<float>(const float*, float*, float*
 template cudaError_t launch_shift_regenerate<double>(const double*, double*, double*, long long,
                                                      long long, int, int, int, int, int, double,
                                                      uint64_t, uint64_t, const double*, cudaStream_t);
+
+PAMD_DEBUG_FETCHER(fragment)
 
 }  // namespace pamd

@@ -21,10 +21,10 @@ __global__ void __launch_bounds__(kElemThreads)
                      R* __restrict__ grad, double* __restrict__ partials, int slot0, R a, R ginv)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    R* xs = reinterpret_cast<R*>(smem_raw);
     __shared__ double red[kElemThreads / 32];
 
     const ElemBlock B = blocks[blockIdx.x];
+    PAMD_ARR(R, xs, reinterpret_cast<R*>(smem_raw), B.n + 2 * B.s);
     const R ak = a * (R)B.k;
     const R* __restrict__ X = pos + B.chain_base;
     const int s = B.s;
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kElemThreads)
 #pragma unroll 8
     for (int q = threadIdx.x; q < cnt; q += kElemThreads) {
         const int e = lo + q;
-        xs[q] = (e >= 0 && e < B.chain_len) ? __ldg(X + e) : R(0);
+        xs[q] = (e >= 0 && e < B.chain_len && PAMD_OK_IDX(e, B.chain_len)) ? __ldg(X + e) : R(0);
     }
     __syncthreads();
 
@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(kElemThreads)
         const R xm = xs[q], x0 = xs[q + s], xp = xs[q + 2 * s];
         const R rp = (e >= s) ? fma_r(ak, xm, x0 - xm) : R(0);
         const R r = (e < rend) ? fma_r(ak, x0, xp - x0) : R(0);
-        if (GRAD && e >= B.own_lo && e < B.own_hi) grad[B.chain_base + e] = fma_r(ak, r, rp - r) * ginv;
+        if (GRAD && e >= B.own_lo && e < B.own_hi && PAMD_OK_IDX(e, B.chain_len))
+            grad[B.chain_base + e] = fma_r(ak, r, rp - r) * ginv;
         if (e >= B.sum_lo) acc = fma_r(r, r, acc);
     }
     const double tot = block_sum((double)acc, red);
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kElemThreads)
     float acc = 0.f;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (long long g = gal + 4LL * threadIdx.x; g < gah; g += 4LL * kElemThreads) {
+        if (!PAMD_OK_IDX(g - base + 3, B.chain_len) || !PAMD_OK_IDX(g - base, B.chain_len)) continue;
         const float4 c = __ldg(reinterpret_cast<const float4*>(pos + g));
         const float4 p = (g - 4 >= sys_lo) ? __ldg(reinterpret_cast<const float4*>(pos + g - 4)) : z4;
         const float4 n = (g + 4 < sys_hi) ? __ldg(reinterpret_cast<const float4*>(pos + g + 4)) : z4;
@@ -137,12 +139,13 @@ __global__ void __launch_bounds__(kElemThreads)
     if ((int)threadIdx.x < nhead + ntail) {
         const long long g = (int)threadIdx.x < nhead ? glo + threadIdx.x : gah + (threadIdx.x - nhead);
         const int le = (int)(g - base);
-        const float x0 = pos[g];
-        const float xm = le >= S ? pos[g - S] : 0.f;
-        const float xp = le < rend ? pos[g + S] : 0.f;
+        const bool ok = PAMD_OK_IDX(le, B.chain_len);
+        const float x0 = ok ? pos[g] : 0.f;
+        const float xm = (le >= S && ok) ? pos[g - S] : 0.f;
+        const float xp = (le < rend && ok) ? pos[g + S] : 0.f;
         const float rp = (le >= S) ? fma_r(ak, xm, x0 - xm) : 0.f;
         const float r = (le < rend) ? fma_r(ak, x0, xp - x0) : 0.f;
-        if (GRAD && le >= B.own_lo && le < B.own_hi) grad[g] = fma_r(ak, r, rp - r) * ginv;
+        if (GRAD && le >= B.own_lo && le < B.own_hi && ok) grad[g] = fma_r(ak, r, rp - r) * ginv;
         if (le >= B.sum_lo) acc = fma_r(r, r, acc);
     }
     const double tot = block_sum((double)acc, red);
@@ -224,5 +227,7 @@ template cudaError_t launch_ho_euler<float>(float*, const float*, int, int, int,
 template cudaError_t launch_ho_euler<double>(double*, const double*, int, int, int, long long, int,
                                              double, double, double, uint64_t, uint64_t,
                                              cudaStream_t);
+
+PAMD_DEBUG_FETCHER(ho)
 
 }  // namespace pamd

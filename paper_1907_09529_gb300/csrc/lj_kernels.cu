@@ -122,7 +122,7 @@ struct LJBlock {
             R dx, dy, dz;
             const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
             if (r2 <= k.rl2) {
-                if (c < cap) nbr[c * NT + tid] = (uint16_t)j;
+                if (c < cap && PAMD_OK_IDX(c * NT + tid, cap * NT)) nbr[c * NT + tid] = (uint16_t)j;
                 ++c;
             }
         }
@@ -154,7 +154,10 @@ struct LJBlock {
     {
         if (!active) return;
         if (!ovf) {
-            for (int m = 0; m < cnt; ++m) f((int)nbr[m * NT + tid]);
+            for (int m = 0; m < cnt; ++m) {
+                const int j = PAMD_OK_IDX(m * NT + tid, cap * NT) ? (int)nbr[m * NT + tid] : i;
+                if (PAMD_OK_IDX(j, N)) f(j);
+            }
         } else {
             for (int j = q; j < N; j += tpp)
                 if (j != i) f(j);
@@ -276,9 +279,10 @@ __device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, u
         R px = R(0), py = R(0), pz = R(0);
         if (pf) {
             const R* Xn = X + (long long)(t + 2) * s;
-            px = __ldg(Xn + threadIdx.x);
-            py = __ldg(Xn + N + threadIdx.x);
-            pz = __ldg(Xn + 2 * N + threadIdx.x);
+            const bool ok = PAMD_OK_IDX((long long)(t + 2) * s + 2 * N + threadIdx.x, (long long)(T + 1) * s);
+            px = ok ? __ldg(Xn + threadIdx.x) : R(0);
+            py = ok ? __ldg(Xn + N + threadIdx.x) : R(0);
+            pz = ok ? __ldg(Xn + 2 * N + threadIdx.x) : R(0);
         }
         if (__syncthreads_or(L.moved(xa, k))) L.build(xa, k);
 
@@ -301,9 +305,11 @@ __device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, u
             L.hvp(xa, rv, rx, ry, rz, k, hx, hy, hz);
             if (lead) {
                 R* Gt = G + (long long)t * s;
-                Gt[i] = fma_r(k.a, hx, rpx - rx) * k.ginv;
-                Gt[N + i] = fma_r(k.a, hy, rpy - ry) * k.ginv;
-                Gt[2 * N + i] = fma_r(k.a, hz, rpz - rz) * k.ginv;
+                if (PAMD_OK_IDX((long long)t * s + 2 * N + i, (long long)(T + 1) * s)) {
+                    Gt[i] = fma_r(k.a, hx, rpx - rx) * k.ginv;
+                    Gt[N + i] = fma_r(k.a, hy, rpy - ry) * k.ginv;
+                    Gt[2 * N + i] = fma_r(k.a, hz, rpz - rz) * k.ginv;
+                }
             }
         }
         rpx = rx;
@@ -317,9 +323,11 @@ __device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, u
     }
     if (GRAD && t1 == T && S.write_nose && lead) {
         R* Gt = G + (long long)T * s;
-        Gt[i] = rpx * k.ginv;
-        Gt[N + i] = rpy * k.ginv;
-        Gt[2 * N + i] = rpz * k.ginv;
+        if (PAMD_OK_IDX((long long)T * s + 2 * N + i, (long long)(T + 1) * s)) {
+            Gt[i] = rpx * k.ginv;
+            Gt[N + i] = rpy * k.ginv;
+            Gt[2 * N + i] = rpz * k.ginv;
+        }
     }
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) partials[I.slot] = tot;
@@ -510,5 +518,7 @@ cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, in
     lj_pair_count_kernel<<<dim3(T + 1, n_chains), 256, smem, st>>>(pos, counts, N, T, sys_offset, k);
     return cudaGetLastError();
 }
+
+PAMD_DEBUG_FETCHER(lj)
 
 }  // namespace pamd

@@ -66,6 +66,16 @@ __device__ __forceinline__ float rsqrt_approx(float v)
     return r;
 }
 
+// Slot o8 = 8 j of a per-particle shared-memory array; a PAMD_DEBUG build checks
+// j < NMAX and sends a bad access to the sink.
+#ifdef PAMD_DEBUG
+#define PAMD_SLOT(T, addr, o8) \
+    (*(debug_in_bounds((o8) >> 3, NMAX, __LINE__) ? reinterpret_cast<T*>(addr) \
+                                                   : reinterpret_cast<T*>(g_pamd_sink)))
+#else
+#define PAMD_SLOT(T, addr, o8) (*reinterpret_cast<T*>(addr))
+#endif
+
 // ------------------------------------------------------------------ shared-memory layout
 // For a block of up to NMAX particles (NMAX = the kernel's maximum block size):
 //   [0, 16 NMAX)        xy[j]  = {x_a, x_b, y_a, y_b} of the positions
@@ -79,13 +89,13 @@ __device__ __forceinline__ float rsqrt_approx(float v)
 template <int NMAX>
 struct Smem {
     unsigned char* base;
-    __device__ float4& xy(int o8) const { return *reinterpret_cast<float4*>(base + 2 * o8); }
+    __device__ float4& xy(int o8) const { return PAMD_SLOT(float4, base + 2 * o8, o8); }
     __device__ float4& rxy(int o8) const
     {
-        return *reinterpret_cast<float4*>(base + 16 * NMAX + 2 * o8);
+        return PAMD_SLOT(float4, base + 16 * NMAX + 2 * o8, o8);
     }
-    __device__ float2& z(int o8) const { return *reinterpret_cast<float2*>(base + 32 * NMAX + o8); }
-    __device__ float2& rz(int o8) const { return *reinterpret_cast<float2*>(base + 40 * NMAX + o8); }
+    __device__ float2& z(int o8) const { return PAMD_SLOT(float2, base + 32 * NMAX + o8, o8); }
+    __device__ float2& rz(int o8) const { return PAMD_SLOT(float2, base + 40 * NMAX + o8, o8); }
     __device__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 48 * NMAX); }
     // staging area of list references {x, y, z, delta}: the residual array
     __device__ float4& ref(int o8) const { return rxy(o8); }
@@ -104,15 +114,15 @@ struct SmemP {
     unsigned char* base;
     __device__ float4& xy(int buf, int o8) const
     {
-        return *reinterpret_cast<float4*>(base + 16 * NMAX * buf + 2 * o8);
+        return PAMD_SLOT(float4, base + 16 * NMAX * buf + 2 * o8, o8);
     }
     __device__ float2& z(int buf, int o8) const
     {
-        return *reinterpret_cast<float2*>(base + 64 * NMAX + 8 * NMAX * buf + o8);
+        return PAMD_SLOT(float2, base + 64 * NMAX + 8 * NMAX * buf + o8, o8);
     }
-    __device__ float4& rxy(int o8) const { return *reinterpret_cast<float4*>(base + 32 * NMAX + 2 * o8); }
-    __device__ float2& rz(int o8) const { return *reinterpret_cast<float2*>(base + 80 * NMAX + o8); }
-    __device__ float4& ref(int o8) const { return *reinterpret_cast<float4*>(base + 48 * NMAX + 2 * o8); }
+    __device__ float4& rxy(int o8) const { return PAMD_SLOT(float4, base + 32 * NMAX + 2 * o8, o8); }
+    __device__ float2& rz(int o8) const { return PAMD_SLOT(float2, base + 80 * NMAX + o8, o8); }
+    __device__ float4& ref(int o8) const { return PAMD_SLOT(float4, base + 48 * NMAX + 2 * o8, o8); }
     __device__ uint32_t* list() const { return reinterpret_cast<uint32_t*>(base + 88 * NMAX); }
 };
 
@@ -281,7 +291,8 @@ struct PairList {
     // Entry c of this thread is half (c & 1) of word (c >> 1) * NT + tid.
     __device__ __forceinline__ void put(int c, int o8) const
     {
-        reinterpret_cast<uint16_t*>(nbr + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
+        if (PAMD_OK_IDX((c >> 1) * NT + tid, (cap >> 1) * NT))
+            reinterpret_cast<uint16_t*>(nbr + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
     }
 
     // Pair test at the staged reference {x, y, z, delta} (residual array) of
@@ -316,7 +327,7 @@ struct PairList {
         int c = 0;
         auto add = [&](bool in, int o8) {
             if (in) {
-                if (c < ocap)
+                if (c < ocap && PAMD_OK_IDX((c >> 1) * NT + tid, (ocap >> 1) * NT))
                     reinterpret_cast<uint16_t*>(outer + (c >> 1) * NT + tid)[c & 1] = (uint16_t)o8;
                 ++c;
             }
@@ -352,7 +363,7 @@ struct PairList {
         if (!oovf) {
             const uint32_t* w = outer + tid;
             for (int m = 0; m < ocnt; m += 2, w += NT) {
-                const uint32_t v = *w;
+                const uint32_t v = PAMD_OK_IDX((m >> 1) * NT + tid, (ocap >> 1) * NT) ? *w : 0u;
                 const int o1 = (int)(v & 0xFFFFu);
                 const bool two = m + 1 < ocnt;
                 const int o2 = two ? (int)(v >> 16) : o1;
@@ -384,11 +395,11 @@ struct PairList {
             const uint32_t* w = nbr + tid;
             int m = 0;
             for (; m + 1 < cnt; m += 2, w += NT) {
-                const uint32_t v = *w;
+                const uint32_t v = PAMD_OK_IDX((m >> 1) * NT + tid, (cap >> 1) * NT) ? *w : 0u;
                 f((int)(v & 0xFFFFu));
                 f((int)(v >> 16));
             }
-            if (m < cnt) f((int)(*w & 0xFFFFu));
+            if (m < cnt) f((int)((PAMD_OK_IDX((m >> 1) * NT + tid, (cap >> 1) * NT) ? *w : 0u) & 0xFFFFu));
         } else {
             for (int j = q; j < N; j += tpp)
                 if (j != i) f(8 * j);
@@ -506,7 +517,7 @@ __device__ __forceinline__ float sq3(float x, float y, float z)
 // float order) to the largest delta.  Called by every thread of the block.
 template <class SM>
 __device__ __forceinline__ void stage_reference(const SM& P, const float* __restrict__ X, int N,
-                                                int lo, int hi, int* dmax_bits)
+                                                int lo, int hi, int* dmax_bits, int n_slices)
 {
     const int s = 3 * N;
     const int c = lo + (hi - 1 - lo) / 2;
@@ -514,12 +525,16 @@ __device__ __forceinline__ void stage_reference(const SM& P, const float* __rest
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         const float* A = X + n;
         const float* C = A + (long long)c * s;
-        const float cx = __ldg(C), cy = __ldg(C + N), cz = __ldg(C + 2 * N);
+        const bool okc = PAMD_OK_IDX((long long)c * s + n + 2 * N, (long long)s * n_slices);
+        const float cx = okc ? __ldg(C) : 0.f, cy = okc ? __ldg(C + N) : 0.f,
+                    cz = okc ? __ldg(C + 2 * N) : 0.f;
         float d2 = 0.0f;
 #pragma unroll 4
         for (int t = lo; t < hi; ++t) {
             const float* Q = A + (long long)t * s;
-            const float ux = __ldg(Q) - cx, uy = __ldg(Q + N) - cy, uz = __ldg(Q + 2 * N) - cz;
+            const bool okq = PAMD_OK_IDX((long long)t * s + n + 2 * N, (long long)s * n_slices);
+            const float ux = (okq ? __ldg(Q) : 0.f) - cx, uy = (okq ? __ldg(Q + N) : 0.f) - cy,
+                        uz = (okq ? __ldg(Q + 2 * N) : 0.f) - cz;
             d2 = fmaxf(d2, __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, ux * ux)));
         }
         // delta rounded up: sqrt and the sums above are within a few ulp
@@ -564,10 +579,11 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
     // Slices (a, a+1) of particle n into registers (a + 1 <= T for every pair).
     auto fetch = [&](int a, int n, float (&v)[6]) {
         const float* A = X + (long long)a * s + n;
+        const bool ok = PAMD_OK_IDX((long long)(a + 1) * s + n + 2 * N, (long long)(T + 1) * s);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            v[2 * c] = __ldg(A + c * N);
-            v[2 * c + 1] = __ldg(A + s + c * N);
+            v[2 * c] = ok ? __ldg(A + c * N) : 0.f;
+            v[2 * c + 1] = ok ? __ldg(A + s + c * N) : 0.f;
         }
     };
     auto store = [&](int n, const float (&v)[6]) {
@@ -599,14 +615,15 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
         float xn = 0.0f, yn = 0.0f, zn = 0.0f;
         if (hasb && L.active) {
             const float* Xb1 = X + (long long)(b + 1) * s + i;
-            xn = __ldg(Xb1);
-            yn = __ldg(Xb1 + N);
-            zn = __ldg(Xb1 + 2 * N);
+            const bool ok = PAMD_OK_IDX((long long)(b + 1) * s + i + 2 * N, (long long)(T + 1) * s);
+            xn = ok ? __ldg(Xb1) : 0.f;
+            yn = ok ? __ldg(Xb1 + N) : 0.f;
+            zn = ok ? __ldg(Xb1 + 2 * N) : 0.f;
         }
 
         if (a == ts) {
             // Outer list over the item's slices [ts, t1].
-            stage_reference(P, X, N, ts, t1 + 1, dmax_bits);
+            stage_reference(P, X, N, ts, t1 + 1, dmax_bits, T + 1);
             __syncthreads();
             L.build_outer(P, k);
             __syncthreads();  // the staged reference is replaced below
@@ -615,7 +632,7 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
         if (b >= win_end) {
             // New window: slices [a, e) (every pair inside has b <= t1 <= T).
             const int e = min(a + W, t1 + 1);
-            stage_reference(P, X, N, a, e, dmax_bits);
+            stage_reference(P, X, N, a, e, dmax_bits, T + 1);
             __syncthreads();
             sk = window_shared_shift(S, k, dmax_bits);
             L.build(P, k);
@@ -661,15 +678,19 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
                 const float2 gz = mul2(fma2(pk(k.a), hz, sub2(pk(rpz, rz.x), rz)), ginv);
                 if (real_a) {
                     float* Ga = G + (long long)a * s + i;
-                    Ga[0] = gx.x;
-                    Ga[N] = gy.x;
-                    Ga[2 * N] = gz.x;
+                    if (PAMD_OK_IDX((long long)a * s + i + 2 * N, (long long)(T + 1) * s)) {
+                        Ga[0] = gx.x;
+                        Ga[N] = gy.x;
+                        Ga[2 * N] = gz.x;
+                    }
                 }
                 if (hasb) {
                     float* Gb = G + (long long)b * s + i;
-                    Gb[0] = gx.y;
-                    Gb[N] = gy.y;
-                    Gb[2 * N] = gz.y;
+                    if (PAMD_OK_IDX((long long)b * s + i + 2 * N, (long long)(T + 1) * s)) {
+                        Gb[0] = gx.y;
+                        Gb[N] = gy.y;
+                        Gb[2 * N] = gz.y;
+                    }
                 }
             }
         }
@@ -682,9 +703,11 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
     }
     if (GRAD && t1 == T && S.write_nose && lead) {
         float* Gt = G + (long long)T * s + i;
-        Gt[0] = rpx * k.ginv;
-        Gt[N] = rpy * k.ginv;
-        Gt[2 * N] = rpz * k.ginv;
+        if (PAMD_OK_IDX((long long)T * s + i + 2 * N, (long long)(T + 1) * s)) {
+            Gt[0] = rpx * k.ginv;
+            Gt[N] = rpy * k.ginv;
+            Gt[2 * N] = rpz * k.ginv;
+        }
     }
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) partials[I.slot] = tot;
@@ -720,10 +743,11 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
 
     auto fetch = [&](int a, int n, float (&v)[6]) {
         const float* A = X + (long long)a * s + n;
+        const bool ok = PAMD_OK_IDX((long long)(a + 1) * s + n + 2 * N, (long long)(T + 1) * s);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            v[2 * c] = __ldg(A + c * N);
-            v[2 * c + 1] = __ldg(A + s + c * N);
+            v[2 * c] = ok ? __ldg(A + c * N) : 0.f;
+            v[2 * c + 1] = ok ? __ldg(A + s + c * N) : 0.f;
         }
     };
     auto store = [&](int buf, int n, const float (&v)[6]) {
@@ -738,7 +762,7 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     auto ensure_window = [&](int a, int last) {
         if (last < win_end) return;
         const int e = min(a + W, t1 + 1);  // > last: last <= a + 3 <= a + W, or last <= t1
-        stage_reference(P, X, N, a, e, dmax_bits);
+        stage_reference(P, X, N, a, e, dmax_bits, T + 1);
         __syncthreads();
         sk = window_shared_shift(S, k, dmax_bits);
         L.build(P, k);
@@ -756,9 +780,10 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
         float xn = 0.0f, yn = 0.0f, zn = 0.0f;
         if (hb) {
             const float* Xb1 = X + (long long)(b + 1) * s + i;
-            xn = __ldg(Xb1);
-            yn = __ldg(Xb1 + N);
-            zn = __ldg(Xb1 + 2 * N);
+            const bool ok = PAMD_OK_IDX((long long)(b + 1) * s + i + 2 * N, (long long)(T + 1) * s);
+            xn = ok ? __ldg(Xb1) : 0.f;
+            yn = ok ? __ldg(Xb1 + N) : 0.f;
+            zn = ok ? __ldg(Xb1 + 2 * N) : 0.f;
         }
         const float4 pxy = P.xy(buf, 8 * i);
         const float2 pz = P.z(buf, 8 * i);
@@ -777,7 +802,7 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     };
 
     // Item-wide outer list.
-    stage_reference(P, X, N, ts, t1 + 1, dmax_bits);
+    stage_reference(P, X, N, ts, t1 + 1, dmax_bits, T + 1);
     __syncthreads();
     L.build_outer(P, k);
     __syncthreads();
@@ -838,15 +863,19 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
             const float2 gz = mul2(fma2(pk(k.a), hz, sub2(pk(rpz, rz.x), rz)), ginv);
             if (real_a) {
                 float* Ga = G + (long long)a * s + i;
-                Ga[0] = gx.x;
-                Ga[N] = gy.x;
-                Ga[2 * N] = gz.x;
+                if (PAMD_OK_IDX((long long)a * s + i + 2 * N, (long long)(T + 1) * s)) {
+                    Ga[0] = gx.x;
+                    Ga[N] = gy.x;
+                    Ga[2 * N] = gz.x;
+                }
             }
             if (hasb) {
                 float* Gb = G + (long long)b * s + i;
-                Gb[0] = gx.y;
-                Gb[N] = gy.y;
-                Gb[2 * N] = gz.y;
+                if (PAMD_OK_IDX((long long)b * s + i + 2 * N, (long long)(T + 1) * s)) {
+                    Gb[0] = gx.y;
+                    Gb[N] = gy.y;
+                    Gb[2 * N] = gz.y;
+                }
             }
         }
         rpx = hasb ? rx.y : rx.x;
@@ -867,9 +896,11 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     }
     if (t1 == T && S.write_nose && lead) {
         float* Gt = G + (long long)T * s + i;
-        Gt[0] = rpx * k.ginv;
-        Gt[N] = rpy * k.ginv;
-        Gt[2 * N] = rpz * k.ginv;
+        if (PAMD_OK_IDX((long long)T * s + i + 2 * N, (long long)(T + 1) * s)) {
+            Gt[0] = rpx * k.ginv;
+            Gt[N] = rpy * k.ginv;
+            Gt[2 * N] = rpz * k.ginv;
+        }
     }
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) partials[I.slot] = tot;
@@ -951,5 +982,7 @@ cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_t
                                  pos, grad, partials, counter, outer, outer_words);
     return cudaGetLastError();
 }
+
+PAMD_DEBUG_FETCHER(lj_paired)
 
 }  // namespace pamd

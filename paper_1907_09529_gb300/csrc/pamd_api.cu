@@ -928,6 +928,37 @@ int pamd_release_cache(void)
     return PAMD_OK;
 }
 
+int pamd_debug_status(int* checked, int* count, int* site, long long* index, long long* bound)
+{
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (cudaDeviceSynchronize() != cudaSuccess) return PAMD_ERR_CUDA;
+#ifdef PAMD_DEBUG
+    const int compiled = 1;
+#else
+    const int compiled = 0;
+#endif
+    int (*const fetch[])(DebugRecord*) = {debug_fetch_ho, debug_fetch_lj, debug_fetch_lj_paired,
+                                          debug_fetch_update, debug_fetch_fragment};
+    int total = 0, first_site = 0;
+    long long first_index = 0, first_bound = 0;
+    for (int f = 0; f < 5; ++f) {
+        DebugRecord r;
+        if (fetch[f](&r)) return PAMD_ERR_CUDA;
+        if (r.count && !total) {
+            first_site = (f + 1) * 100000 + r.site;
+            first_index = r.index;
+            first_bound = r.bound;
+        }
+        total += r.count;
+    }
+    if (checked) *checked = compiled;
+    if (count) *count = total;
+    if (site) *site = first_site;
+    if (index) *index = first_index;
+    if (bound) *bound = first_bound;
+    return PAMD_OK;
+}
+
 int pamd_pipeline_timeline(float* ms, int max_entries, int* n_chunks)
 {
     std::lock_guard<std::mutex> lk(g_mutex);

@@ -9,6 +9,79 @@
 
 namespace pamd {
 
+// ------------------------------------------------------------------ debug bounds checks
+// In a build with -DPAMD_DEBUG (libpamd_debug.so) the kernels' array accesses
+// made through PAMD_ARR arrays, pamd::at() and the shared-memory accessors are
+// bounds-checked: an index outside [0, n) records (source line, index, bound) in
+// this translation unit's device record -- the first one wins -- and the access
+// goes to a sink instead (a load then reads garbage, nothing outside the arrays
+// is touched, nothing traps).  pamd_debug_status() collects and clears the
+// records.  Without PAMD_DEBUG every check compiles away.
+struct DebugRecord {
+    int count;        // out-of-bounds accesses seen
+    int site;         // source line of the first
+    long long index;  // its index
+    long long bound;  // the array's extent
+};
+#ifdef PAMD_DEBUG
+static __device__ DebugRecord g_pamd_debug;
+static __device__ __align__(32) unsigned char g_pamd_sink[64];
+
+__device__ __forceinline__ bool debug_in_bounds(long long i, long long n, int site)
+{
+    if (i >= 0 && i < n) return true;
+    if (atomicAdd(&g_pamd_debug.count, 1) == 0) {
+        g_pamd_debug.site = site;
+        g_pamd_debug.index = i;
+        g_pamd_debug.bound = n;
+    }
+    return false;
+}
+
+// An array with its extent: indexing checks the bound.
+template <typename T>
+struct ChkArr {
+    T* p;
+    long long n;
+    int site;
+    __device__ __forceinline__ T& operator[](long long i) const
+    {
+        return debug_in_bounds(i, n, site) ? p[i] : *reinterpret_cast<T*>(g_pamd_sink);
+    }
+    __device__ __forceinline__ ChkArr operator+(long long k) const { return ChkArr{p + k, n - k, site}; }
+    __device__ __forceinline__ operator T*() const { return p; }
+};
+#define PAMD_ARR(T, name, ptr, extent) ::pamd::ChkArr<T> name{(ptr), (long long)(extent), __LINE__}
+#define PAMD_AT(ptr, i, extent) \
+    (*(::pamd::debug_in_bounds((long long)(i), (long long)(extent), __LINE__) ? &(ptr)[i] \
+        : reinterpret_cast<decltype(&(ptr)[0])>(::pamd::g_pamd_sink)))
+
+// Guard of one access: true when 0 <= i < n (a failure is recorded).
+#define PAMD_OK_IDX(i, n) ::pamd::debug_in_bounds((long long)(i), (long long)(n), __LINE__)
+
+// Host side: this translation unit's record, copied out and cleared.
+static inline int debug_fetch_record(DebugRecord* out)
+{
+    if (cudaMemcpyFromSymbol(out, g_pamd_debug, sizeof(DebugRecord)) != cudaSuccess) return -1;
+    const DebugRecord zero{0, 0, 0, 0};
+    return cudaMemcpyToSymbol(g_pamd_debug, &zero, sizeof(DebugRecord)) == cudaSuccess ? 0 : -1;
+}
+#define PAMD_DEBUG_FETCHER(tu) \
+    int debug_fetch_##tu(DebugRecord* out) { return debug_fetch_record(out); }
+#else
+#define PAMD_OK_IDX(i, n) true
+#define PAMD_ARR(T, name, ptr, extent) T* name = (ptr)
+#define PAMD_AT(ptr, i, extent) ((ptr)[i])
+#define PAMD_DEBUG_FETCHER(tu) \
+    int debug_fetch_##tu(DebugRecord* out) { *out = DebugRecord{0, 0, 0, 0}; return 0; }
+#endif
+// Per translation unit: its record (zeros in a build without the checks).
+int debug_fetch_ho(DebugRecord* out);
+int debug_fetch_lj(DebugRecord* out);
+int debug_fetch_lj_paired(DebugRecord* out);
+int debug_fetch_update(DebugRecord* out);
+int debug_fetch_fragment(DebugRecord* out);
+
 // ------------------------------------------------------------------ vector types
 struct alignas(32) double4a {
     double x, y, z, w;

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kElemThreads)
         for (int l = 0; l < 4; ++l) {
             const int e = B.e0 + 4 * gq + l;
             if (e >= B.e0 + B.n) break;
+            if (!PAMD_OK_IDX(e, B.chain_len)) continue;
             const R x = pos[base + e];
             if (e < B.s || e >= B.own_hi) {  // fixed tail x_0, or a time-slab halo
                 prop[base + e] = x;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kElemThreads)
 #pragma unroll 4
     for (int q = threadIdx.x; q < B.n; q += kElemThreads) {
         const int e = B.e0 + q;
-        if (e < B.s || e >= B.own_hi) continue;
+        if (e < B.s || e >= B.own_hi || !PAMD_OK_IDX(e, B.chain_len)) continue;
         const R x = pos[base + e], xp = prop[base + e], gp = grad_prop[base + e];
         const R b = fma_r(h, gp, x - xp);
         acc = fma_r(b, b, acc);
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(kElemThreads)
 #pragma unroll 4
     for (int q = threadIdx.x; q < B.n; q += kElemThreads) {
         const long long e = base + B.e0 + q;
+        if (!PAMD_OK_IDX(B.e0 + q, B.chain_len)) continue;
         pos[e] = prop[e];
         grad[e] = grad_prop[e];
     }
@@ -280,5 +282,7 @@ cudaError_t launch_normals(uint64_t seed, uint64_t counter, uint32_t stream_id, 
         seed, counter, stream_id, chain, e0, n, out);
     return cudaGetLastError();
 }
+
+PAMD_DEBUG_FETCHER(update)
 
 }  // namespace pamd
