@@ -166,6 +166,29 @@ int pamd_action(const pamd_problem* prob, const void* pos, double* S, void* stre
 int pamd_action_grad(const pamd_problem* prob, const void* pos, double* S, void* grad,
                      void* stream);
 
+/* Action and path gradient with the hard-sphere path bias of the paper's
+ * Lennard-Jones runs (Sec. IV.B): at slice t the pair potential is
+ *     V(r; sigma_HS(t)) = U(r) + U_HS(r; sigma_HS(t)),
+ *     U_HS = +inf for r <= sigma_HS(t), 0 beyond,
+ * U the cut-and-force-shifted Lennard-Jones potential of Eq. (11) and sigma_HS(t)
+ * a schedule along the path supplied by the caller.  U_HS adds no force where it
+ * is finite, so:
+ *   S[c]  = the Lennard-Jones action of chain c (as pamd_action_grad), or +inf if
+ *           at some slice t = 0..T a pair within the cutoff lies at
+ *           r <= sigma_HS(t) (minimum image, decided in the path's precision by
+ *           the rule of pamd_lj_pair_counts, with the squared radius rounded to
+ *           the element type; a radius <= 0 tests nothing, one >= rc acts as rc);
+ *   grad  = the Lennard-Jones gradient (written as by pamd_action_grad), or NULL
+ *           for the action only.
+ *   sigma_hs : device double array: for every PAMD_LJ system in order, its T+1
+ *           radii sigma_HS(0..T) (harmonic systems take none).
+ * Harmonic systems get their plain action.  Device pointers only
+ * (PAMD_ERR_ARG otherwise).  Combined with the pamd_mala_* pieces, a proposal
+ * with an overlapping pair has S' = +inf and is rejected.  The trial paths the
+ * paper draws from a hard-sphere propagator are not part of this library. */
+int pamd_action_grad_hs(const pamd_problem* prob, const void* pos, const double* sigma_hs,
+                        double* S, void* grad, void* stream);
+
 /* n_updates successive whole-path Metropolis-adjusted Langevin updates of
  * every chain, consuming the path gradient; the tail slice x_0 is held
  * fixed and the update is accepted by the Metropolis-Hastings test (the

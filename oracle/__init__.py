@@ -110,6 +110,9 @@ def _load():
             "or_uniform": (c_double, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_uint32]),
             "or_pair_count_f32": (c_ll, [c_int, c_double, c_double, _F]),
+            "or_hs_first_overlap": (c_int, [ctypes.POINTER(Potential), c_int, c_int, c_int, _D,
+                                            _D]),
+            "or_hs_overlap_f32": (c_int, [c_int, c_double, c_double, c_double, _F]),
             "or_num_threads_available": (c_int, []),
         }
         for name, (res, args) in sig.items():
@@ -336,3 +339,35 @@ def pair_count_f32(box: float, rc: float, x: np.ndarray) -> int:
     d, N = x.shape
     assert d == 3
     return int(_load().or_pair_count_f32(N, float(box), float(rc), x.ctypes.data_as(_F)))
+
+
+def hs_first_overlap(pot: Potential, pos: np.ndarray, sigma_hs) -> int:
+    """First slice t of pos [T+1][d][N] with a pair at r <= sigma_hs[t] (within the
+    cutoff), or -1: the slices where the hard-sphere bias of the paper's LJ runs
+    (Sec. IV.B) is infinite."""
+    pos = _f64(pos)
+    T = pos.shape[0] - 1
+    _, d, N = pos.shape
+    sig = np.ascontiguousarray(sigma_hs, dtype=np.float64)
+    assert sig.shape == (T + 1,)
+    return int(_load().or_hs_first_overlap(ctypes.byref(pot), N, d, T, _d(pos), _d(sig)))
+
+
+def action_grad_hs(pot: Potential, pos: np.ndarray, sigma_hs, D: float, beta: float, dt: float,
+                   nthreads: int = 1):
+    """Action and gradient with the hard-sphere path bias: the LJ action, or +inf
+    if any slice t has a pair at r <= sigma_hs[t]; the gradient is the LJ one
+    (the bias adds no force where it is finite)."""
+    S, g = action_grad(pot, pos, D, beta, dt, nthreads=nthreads)
+    if hs_first_overlap(pot, pos, sigma_hs) >= 0:
+        S = float("inf")
+    return S, g
+
+
+def hs_overlap_f32(box: float, rc: float, sigma: float, x: np.ndarray) -> bool:
+    """The hard-sphere overlap decision at one slice x[3][N] (float32) in single
+    precision, by the GPU's documented rule."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    N = x.shape[-1]
+    return bool(_load().or_hs_overlap_f32(N, float(box), float(rc), float(sigma),
+                                          x.ctypes.data_as(_F)))

@@ -655,6 +655,62 @@ long long or_pair_count_f32(int N, double box, double rc, const float* x)
     return count;
 }
 
+/* ---------------------------------------------------------------- */
+/* Hard-sphere path bias of the paper's Lennard-Jones runs (Sec. IV.B): slice t
+ * of the path carries, besides the pair potential U of Eq. (11), the pair
+ * potential U_HS(r; sigma_t) = +inf for r <= sigma_t and 0 beyond, sigma_t the
+ * schedule's value at that slice.  Only pairs within the cutoff rc are tested
+ * (a sigma_t at or above rc acts as rc).  The hard-sphere term adds no force
+ * where it is finite, so it changes the action only through the +inf of a path
+ * with such a pair at any slice t = 0..T.  Returns the first such slice, or -1.
+ * All pairs, minimum image, double precision. */
+int or_hs_first_overlap(const or_potential* p, int N, int d, int T, const double* pos,
+                        const double* sigma_hs)
+{
+    int M = d * N;
+    for (int t = 0; t <= T; ++t) {
+        double lim = sigma_hs[t] < p->rc ? sigma_hs[t] : p->rc;
+        if (!(lim > 0.0)) continue;
+        const double* x = pos + (size_t)t * M;
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) {
+                double r2 = 0.0;
+                for (int c = 0; c < d; ++c) {
+                    double dx = min_image(p, x[c * N + i] - x[c * N + j]);
+                    r2 += dx * dx;
+                }
+                if (r2 <= lim * lim) return t;
+            }
+    }
+    return -1;
+}
+
+/* The same decision at one slice in the kernels' single precision (an integer
+ * outcome decided in floating point, compared bit for bit): the pair vector by
+ * the rule of or_pair_count_f32, included iff r2 <= rc2f (the cutoff) and
+ * r2 <= (float)(sigma * sigma).  Returns 1 if some pair i < j is included. */
+int or_hs_overlap_f32(int N, double box, double rc, double sigma, const float* x)
+{
+    float Lf = (float)box;
+    float iLf = 1.0f / Lf;
+    float rcf = (float)rc;
+    float rc2f = rcf * rcf;
+    float hs2 = (float)(sigma * sigma);
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            float dxyz[3];
+            for (int c = 0; c < 3; ++c) {
+                float dx = x[c * N + i] - x[c * N + j];
+                float sh = fmaf(dx, iLf, 12582912.0f) - 12582912.0f;
+                dxyz[c] = fmaf(-Lf, sh, dx);
+            }
+            float xx = dxyz[0] * dxyz[0];
+            float r2 = fmaf(dxyz[2], dxyz[2], fmaf(dxyz[1], dxyz[1], xx));
+            if (r2 <= rc2f && r2 <= hs2) return 1;
+        }
+    return 0;
+}
+
 int or_num_threads_available(void)
 {
 #ifdef _OPENMP

@@ -21,7 +21,7 @@ from ._lib import (PAMD_FLAG_HO_EXACT_PROPAGATOR, PAMD_FLAG_ONE_CHAIN_PER_LAUNCH
                    PamdError, pamd_action, pamd_action_grad, pamd_device_status, pamd_euler_reference,
                    pamd_event, pamd_fragment_mc, pamd_shift_regenerate,
                    pamd_lj_pair_counts, pamd_normals, pamd_path_update, pamd_philox,
-                   pamd_cache_stats, pamd_mala_accept, pamd_mala_commit, pamd_mala_propose,
+                   pamd_action_grad_hs, pamd_cache_stats, pamd_mala_accept, pamd_mala_commit, pamd_mala_propose,
                    pamd_mala_reverse, pamd_release_cache, pamd_tune, pamd_version)
 
 __all__ = [
@@ -32,7 +32,8 @@ __all__ = [
     "pamd_version", "pamd_device_status", "device_status", "pamd_fragment_mc", "fragment_mc",
     "fragment_slots", "pamd_shift_regenerate", "pamd_event", "pamd_cache_stats", "cache_stats",
     "mala_propose", "mala_reverse", "mala_accept", "mala_commit", "pamd_mala_propose",
-    "pamd_mala_reverse", "pamd_mala_accept", "pamd_mala_commit",
+    "pamd_mala_reverse", "pamd_mala_accept", "pamd_mala_commit", "action_grad_hs",
+    "pamd_action_grad_hs",
 ]
 
 ALIGN = 8  # system offsets are rounded to 8 elements (>= 16 bytes)
@@ -160,6 +161,22 @@ def action_grad(p: Problem, pos: torch.Tensor, S: Optional[torch.Tensor] = None,
     if grad is None:
         grad = torch.zeros_like(pos)  # padding between systems stays defined
     pamd_action_grad(p.ref, _ptr(pos), _ptr(S), _ptr(grad), _stream(pos, stream))
+    return S, grad
+
+
+def action_grad_hs(p: Problem, pos: torch.Tensor, sigma_hs: torch.Tensor,
+                   S: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None,
+                   with_grad: bool = True, stream=None):
+    """Action (+inf where a pair lies within its slice's hard-sphere radius) and
+    gradient with the hard-sphere path bias of the paper's LJ runs;
+    sigma_hs: float64 device tensor, T+1 radii per LJ system in order."""
+    _check_buf(p, pos, "pos")
+    if S is None:
+        S = torch.empty(p.n_chains, dtype=torch.float64, device=pos.device)
+    if grad is None and with_grad:
+        grad = torch.zeros_like(pos)
+    pamd_action_grad_hs(p.ref, _ptr(pos), _ptr(sigma_hs.contiguous()), _ptr(S), _ptr(grad),
+                        _stream(pos, stream))
     return S, grad
 
 

@@ -39,7 +39,7 @@ EXPORTS = (
     "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate", "pamd_event",
     "pamd_cache_stats", "pamd_fp32_fma_probe", "pamd_pipeline_timeline",
     "pamd_mala_propose", "pamd_mala_reverse", "pamd_mala_accept", "pamd_mala_commit",
-    "pamd_debug_status",
+    "pamd_debug_status", "pamd_action_grad_hs",
 )
 
 #: Scratch capacity of pamd_ho_action_grad_noalloc (block sums; one per 4096 elements).
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
             "pamd_device_status": (ctypes.c_int, [_VP]),
             "pamd_cache_stats": (ctypes.c_int, [_VP, _VP]),
             "pamd_debug_status": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+            "pamd_action_grad_hs": (ctypes.c_int, [_PP, _VP, _VP, _VP, _VP, _VP]),
             "pamd_mala_propose": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.c_double, u64, u64,
                                                  _VP, _VP, _VP]),
             "pamd_mala_reverse": (ctypes.c_int, [_PP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
@@ -150,6 +151,10 @@ def pamd_action(prob, pos, S, stream):
 
 def pamd_action_grad(prob, pos, S, grad, stream):
     return _call("pamd_action_grad", prob, pos, S, grad, stream)
+
+
+def pamd_action_grad_hs(prob, pos, sigma_hs, S, grad, stream):
+    return _call("pamd_action_grad_hs", prob, pos, sigma_hs, S, grad, stream)
 
 
 def pamd_path_update(prob, pos, grad, S, h, n_updates, seed, counter, noise, log_u, n_accepted,

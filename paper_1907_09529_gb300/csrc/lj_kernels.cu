@@ -167,14 +167,19 @@ struct LJBlock {
     // F(x) of particle i (complete in every thread of the group).  Single
     // precision is branch-free (every list entry evaluated, masked by the cutoff
     // test); double precision skips the costly math outside the cutoff.
-    __device__ void force(const V4* __restrict__ buf, const LJK<R>& k, R& fx, R& fy, R& fz) const
+    // ov (non-null: the hard-sphere path bias is on): raised when a pair within the
+    // cutoff lies within the squared hard-sphere radius hs2v of this slice.
+    __device__ void force(const V4* __restrict__ buf, const LJK<R>& k, R& fx, R& fy, R& fz,
+                          R hs2v = R(-1), bool* ov = nullptr) const
     {
         fx = fy = fz = R(0);
         if (active) {
             const V4 p = buf[i];
+            bool o = false;
             for_each_candidate([&](int j) {
                 R dx, dy, dz;
                 const R r2 = pair_r2<R>(p.x, p.y, p.z, buf[j], k, dx, dy, dz);
+                if (ov && r2 <= k.rc2 && r2 <= hs2v) o = true;
                 if (sizeof(R) == 8 && !(r2 <= k.rc2)) return;
                 R ir2, u, ir6;
                 R fs = pair_fs<R>(r2, k, ir2, u, ir6);
@@ -183,6 +188,7 @@ struct LJBlock {
                 fy = fma_r(fs, dy, fy);
                 fz = fma_r(fs, dz, fz);
             });
+            if (ov) *ov |= o;
         }
         group_sum(fx, fy, fz);
     }
@@ -228,8 +234,10 @@ __device__ __forceinline__ void load_slice(vec4_t<R>* buf, const R* __restrict__
 template <typename R, bool GRAD>
 __device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, unsigned char* smem,
                                         int nmax, const R* __restrict__ pos, R* __restrict__ grad,
-                                        double* __restrict__ partials, double* red)
+                                        double* __restrict__ partials, double* red,
+                                        const R* __restrict__ hs2, int* __restrict__ overlap)
 {
+    bool ov = false;  // hard-sphere path bias (hs2 non-null): a pair within its slice's radius
     using V4 = vec4_t<R>;
     const int N = S.N;
     V4* xa = reinterpret_cast<V4*>(smem);
@@ -287,7 +295,10 @@ __device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, u
         if (__syncthreads_or(L.moved(xa, k))) L.build(xa, k);
 
         R fx, fy, fz;
-        L.force(xa, k, fx, fy, fz);
+        if (hs2)
+            L.force(xa, k, fx, fy, fz, hs2[S.hs_off + t], &ov);
+        else
+            L.force(xa, k, fx, fy, fz);
         R rx = R(0), ry = R(0), rz = R(0);
         if (L.active) {
             const V4 p0 = xa[i], p1 = xb[i];
@@ -329,6 +340,7 @@ __device__ __forceinline__ void lj_item(const LJItem& I, const LJSysDev<R>& S, u
             Gt[2 * N + i] = rpz * k.ginv;
         }
     }
+    if (hs2 && __syncthreads_or(ov) && threadIdx.x == 0) atomicOr(overlap + S.chain0 + I.chain, 1);
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) partials[I.slot] = tot;
 }
@@ -338,7 +350,8 @@ template <typename R, bool GRAD, int MAXT>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
     lj_action_kernel(const LJItem* __restrict__ items, int n_items,
                      const LJSysDev<R>* __restrict__ systems, int nmax, const R* __restrict__ pos,
-                     R* __restrict__ grad, double* __restrict__ partials, int* __restrict__ counter)
+                     R* __restrict__ grad, double* __restrict__ partials, int* __restrict__ counter,
+                     const R* __restrict__ hs2, int* __restrict__ overlap)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double red[32];
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 512 ? 2 : 1))
         if (it >= n_items) break;
         const LJItem I = items[it];
         const LJSysDev<R> S = systems[I.sys];
-        lj_item<R, GRAD>(I, S, smem_raw, nmax, pos, grad, partials, red);
+        lj_item<R, GRAD>(I, S, smem_raw, nmax, pos, grad, partials, red, hs2, overlap);
     }
 }
 
@@ -382,7 +395,8 @@ int lj_blocks_per_sm(int NT, size_t smem, bool with_grad)
 template <typename R>
 cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_table, int nmax,
                             const R* pos, R* grad, double* partials, int* counter, int NT,
-                            size_t smem, int grid, bool with_grad, cudaStream_t st)
+                            size_t smem, int grid, bool with_grad, cudaStream_t st, const R* hs2,
+                            int* overlap)
 {
     if (n_items <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
@@ -391,7 +405,7 @@ cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_ta
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, smem, st>>>(items, n_items, static_cast<const LJSysDev<R>*>(sys_table), nmax,
-                                 pos, grad, partials, counter);
+                                 pos, grad, partials, counter, hs2, overlap);
     return cudaGetLastError();
 }
 
@@ -399,10 +413,94 @@ template int lj_blocks_per_sm<float>(int, size_t, bool);
 template int lj_blocks_per_sm<double>(int, size_t, bool);
 template cudaError_t launch_lj_items<float>(const LJItem*, int, const void*, int, const float*,
                                             float*, double*, int*, int, size_t, int, bool,
-                                            cudaStream_t);
+                                            cudaStream_t, const float*, int*);
 template cudaError_t launch_lj_items<double>(const LJItem*, int, const void*, int, const double*,
                                              double*, double*, int*, int, size_t, int, bool,
-                                             cudaStream_t);
+                                             cudaStream_t, const double*, int*);
+
+// ------------------------------------------------------------------ hard-sphere path bias
+// Squared hard-sphere radii in the path's precision (a radius <= 0: no bias at
+// that slice, -1).
+template <typename R>
+__global__ void hs_square_kernel(const double* __restrict__ sigma, R* __restrict__ hs2, long long n)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const double v = sigma[q];
+    hs2[q] = v > 0.0 ? (R)(v * v) : R(-1);
+}
+
+template <typename R>
+cudaError_t launch_hs_square(const double* sigma, R* hs2, long long n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    hs_square_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sigma, hs2, n);
+    return cudaGetLastError();
+}
+
+// The bias at slice t of every chain of one system, all pairs (the force walks
+// test the slices whose forces they evaluate, 0..T-1; this covers the nose T):
+// a pair i < j within the cutoff and within the squared radius hs2[t] sets the
+// chain's overlap flag.  One CTA per chain; the pair vector by pair_r2's rule.
+template <typename R>
+__global__ void lj_hs_slice_kernel(const R* __restrict__ pos, int N, int T, int t, long long sys_offset,
+                                   int chain0, const LJK<R> k, const R* __restrict__ hs2t,
+                                   int* __restrict__ overlap)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    vec4_t<R>* xs = reinterpret_cast<vec4_t<R>*>(smem_raw);
+    const int chain = blockIdx.x, s = 3 * N;
+    const R h2 = *hs2t;
+    if (!(h2 >= R(0))) return;  // no bias at this slice (uniform over the block)
+    load_slice<R>(xs, pos + sys_offset + (long long)chain * (T + 1) * s + (long long)t * s, N);
+    __syncthreads();
+    bool o = false;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const vec4_t<R> p = xs[i];
+        for (int j = i + 1; j < N; ++j) {
+            R dx, dy, dz;
+            const R r2 = pair_r2<R>(p.x, p.y, p.z, xs[j], k, dx, dy, dz);
+            o |= (r2 <= k.rc2) & (r2 <= h2);
+        }
+    }
+    if (__syncthreads_or(o) && threadIdx.x == 0) atomicOr(overlap + chain0 + chain, 1);
+}
+
+template <typename R>
+cudaError_t launch_lj_hs_slice(const R* pos, const void* sys_entry_host, int n_chains, int t,
+                               const R* hs2t, int* overlap, cudaStream_t st)
+{
+    const LJSysDev<R> S = *static_cast<const LJSysDev<R>*>(sys_entry_host);
+    if (n_chains <= 0) return cudaSuccess;
+    const size_t smem = sizeof(vec4_t<R>) * (size_t)S.N;
+    auto kern = lj_hs_slice_kernel<R>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return cudaErrorInvalidValue;
+    kern<<<n_chains, 256, smem, st>>>(pos, S.N, S.T, t, S.off, S.chain0, S.k, hs2t, overlap);
+    return cudaGetLastError();
+}
+
+// A chain whose path has an overlapping pair gets S = +inf.
+__global__ void hs_fixup_kernel(double* __restrict__ S, const int* __restrict__ overlap, int n)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n && overlap[c]) S[c] = __longlong_as_double(0x7ff0000000000000LL);
+}
+
+cudaError_t launch_hs_fixup(double* S, const int* overlap, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    hs_fixup_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, overlap, n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_hs_square<float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_hs_square<double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_lj_hs_slice<float>(const float*, const void*, int, int, const float*,
+                                               int*, cudaStream_t);
+template cudaError_t launch_lj_hs_slice<double>(const double*, const void*, int, int, const double*,
+                                                int*, cudaStream_t);
 
 // ------------------------------------------------------------------ Euler-Maruyama (Eq. (2))
 // One CTA per chain, sequential in time; forces as in the action kernel.

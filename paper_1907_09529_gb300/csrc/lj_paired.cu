@@ -417,21 +417,28 @@ struct PairList {
 
     // F(x_a), F(x_b) of particle i (complete in every thread of the group).
     // SK: the window allows one image shift per pair (pair_vec_shift).
-    template <bool SK>
-    __device__ void force(const Smem<NMAX>& P, const K2& k, float2& fx, float2& fy, float2& fz) const
+    // HS: also raise `ov` when a pair lies within the hard-sphere radii (squared:
+    // hs2 for the two steps) of the path bias.
+    template <bool SK, bool HS = false>
+    __device__ void force(const Smem<NMAX>& P, const K2& k, float2& fx, float2& fy, float2& fz,
+                          float2 hs2 = float2(), bool* ov = nullptr) const
     {
         fx = fy = fz = pk(0.0f);
         if (active) {
             const float4 pxy = P.xy(8 * i);
             const float2 xi = pk(pxy.x, pxy.y), yi = pk(pxy.z, pxy.w), zi = P.z(8 * i);
+            bool o = false;
             for_each_candidate([&](int o8) {
                 float2 dx, dy, dz, ri, ir2, ir6, ir8;
                 pair_vec_sel<SK>(xi, yi, zi, P.xy(o8), P.z(o8), k, dx, dy, dz);
-                const float2 fs = pair_fs(pair_r2(dx, dy, dz, k), k, ri, ir2, ir6, ir8);
+                const float2 r2 = pair_r2(dx, dy, dz, k);
+                if (HS) o |= (r2.x <= hs2.x) | (r2.y <= hs2.y);
+                const float2 fs = pair_fs(r2, k, ri, ir2, ir6, ir8);
                 fx = fma2(fs, dx, fx);
                 fy = fma2(fs, dy, fy);
                 fz = fma2(fs, dz, fz);
             });
+            if (HS) *ov |= o;
         }
         group_sum(fx, fy, fz);
     }
@@ -463,13 +470,17 @@ struct PairList {
     // image shift per list entry, rounded at the first slice walked and applied to
     // all four (the window keeps every particle within (L/2 - rc)/4 of its
     // reference, so the shift is the nearest image's at each of them).
-    template <bool DO_H, bool DO_F, bool SK>
+    // HS: also raise `ov` when a pair of the force walk lies within the hard-sphere
+    // radii (squared: hs2 for the force pair's two steps) of the path bias.
+    template <bool DO_H, bool DO_F, bool SK, bool HS = false>
     __device__ void combined(const SmemP<NMAX>& P, int hb, int fb, float2 vix, float2 viy,
                              float2 viz, const K2& k, float2& hx, float2& hy, float2& hz,
-                             float2& fx, float2& fy, float2& fz) const
+                             float2& fx, float2& fy, float2& fz, float2 hs2 = float2(),
+                             bool* ov = nullptr) const
     {
         hx = hy = hz = fx = fy = fz = pk(0.0f);
         if (active) {
+            bool o = false;
             const float4 hxy = P.xy(hb, 8 * i);
             const float2 hxi = pk(hxy.x, hxy.y), hyi = pk(hxy.z, hxy.w), hzi = P.z(hb, 8 * i);
             const float4 fxy = P.xy(fb, 8 * i);
@@ -494,12 +505,15 @@ struct PairList {
                         pair_vec_shift(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz, sx, sy, sz);
                     else
                         pair_vec(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz);
-                    const float2 fs = pair_fs(pair_r2(dx, dy, dz, k), k, ri, ir2, ir6, ir8);
+                    const float2 r2 = pair_r2(dx, dy, dz, k);
+                    if (HS) o |= (r2.x <= hs2.x) | (r2.y <= hs2.y);
+                    const float2 fs = pair_fs(r2, k, ri, ir2, ir6, ir8);
                     fx = fma2(fs, dx, fx);
                     fy = fma2(fs, dy, fy);
                     fz = fma2(fs, dz, fz);
                 }
             });
+            if (HS && DO_F) *ov |= o;
         }
         if (DO_H) group_sum(hx, hy, hz);
         if (DO_F) group_sum(fx, fy, fz);
@@ -555,11 +569,12 @@ __device__ __forceinline__ bool window_shared_shift(const LJSysDev<float>& S, co
 }
 
 // One work item: steps [t0, t1) of one chain.
-template <bool GRAD, int NMAX>
+template <bool GRAD, int NMAX, bool HS>
 __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<float>& S,
                                             unsigned char* smem, const float* __restrict__ pos,
                                             float* __restrict__ grad, double* __restrict__ partials,
-                                            double* red, uint32_t* outer, int* dmax_bits)
+                                            double* red, uint32_t* outer, int* dmax_bits,
+                                            const float* __restrict__ hs2, int* __restrict__ overlap)
 {
     const int N = S.N;
     const Smem<NMAX> P{smem};
@@ -603,6 +618,7 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
     const int W = max(2, S.window);
     int win_end = ts;  // slices [.., win_end) are covered by the current list
     bool sk = false;   // the current window allows one image shift per entry
+    bool ov = false;   // a pair within the hard-sphere radius of its slice (HS)
 
     for (int a = ts; a < t1; a += 2) {
         const int b = a + 1;
@@ -642,10 +658,11 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
         }
 
         float2 fx, fy, fz;
+        const float2 hsab = HS ? pk(hs2[S.hs_off + a], hs2[S.hs_off + b]) : float2();
         if (sk)
-            L.template force<true>(P, k, fx, fy, fz);
+            L.template force<true, HS>(P, k, fx, fy, fz, hsab, &ov);
         else
-            L.template force<false>(P, k, fx, fy, fz);
+            L.template force<false, HS>(P, k, fx, fy, fz, hsab, &ov);
         float2 rx = pk(0.0f), ry = pk(0.0f), rz = pk(0.0f);
         if (L.active) {
             const float4 pxy = P.xy(8 * i);
@@ -709,6 +726,7 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
             Gt[2 * N] = rpz * k.ginv;
         }
     }
+    if (HS && __syncthreads_or(ov) && threadIdx.x == 0) atomicOr(overlap + S.chain0 + I.chain, 1);
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) partials[I.slot] = tot;
 }
@@ -719,12 +737,14 @@ __device__ __forceinline__ void paired_item(const LJItem& I, const LJSysDev<floa
 // positions of two pairs are resident.  Window lists cover two consecutive pairs;
 // windows are at least 4 steps long and overlap by one pair.  Every sum is the
 // same as in paired_item.
-template <int NMAX>
+template <int NMAX, bool HS>
 __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev<float>& S,
                                                  unsigned char* smem, const float* __restrict__ pos,
                                                  float* __restrict__ grad,
                                                  double* __restrict__ partials, double* red,
-                                                 uint32_t* outer, int* dmax_bits)
+                                                 uint32_t* outer, int* dmax_bits,
+                                                 const float* __restrict__ hs2,
+                                                 int* __restrict__ overlap)
 {
     const int N = S.N;
     const SmemP<NMAX> P{smem};
@@ -757,6 +777,9 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     const int W = max(4, S.window);
     int win_end = ts;
     bool sk = false;  // the current window allows one image shift per entry
+    bool ov = false;  // a pair within the hard-sphere radius of its slice (HS)
+    // squared hard-sphere radii of slices a, a+1 (the force pair starting at a)
+    auto hs_pair = [&](int a) { return HS ? pk(hs2[S.hs_off + a], hs2[S.hs_off + a + 1]) : float2(); };
     // Window list covering slices up to `last` (the b slice of the later of the two
     // pairs the next walk touches), starting at slice a.
     auto ensure_window = [&](int a, int last) {
@@ -827,11 +850,11 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     {
         float2 hx, hy, hz, fx, fy, fz;
         if (sk)
-            L.template combined<false, true, true>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx, hy,
-                                                   hz, fx, fy, fz);
+            L.template combined<false, true, true, HS>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx,
+                                                       hy, hz, fx, fy, fz, hs_pair(ts), &ov);
         else
-            L.template combined<false, true, false>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx, hy,
-                                                    hz, fx, fy, fz);
+            L.template combined<false, true, false, HS>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx,
+                                                        hy, hz, fx, fy, fz, hs_pair(ts), &ov);
         residual(0, ts, fx, fy, fz, rx, ry, rz);
         account(ts, rx, ry, rz);
     }
@@ -850,9 +873,11 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
 
         float2 hx, hy, hz, fx, fy, fz;
         if (next && sk)
-            L.template combined<true, true, true>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+            L.template combined<true, true, true, HS>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy,
+                                                      fz, hs_pair(a + 2), &ov);
         else if (next)
-            L.template combined<true, true, false>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+            L.template combined<true, true, false, HS>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy,
+                                                       fz, hs_pair(a + 2), &ov);
         else if (sk)
             L.template combined<true, false, true>(P, cur, cur, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
         else
@@ -902,18 +927,22 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
             Gt[2 * N] = rpz * k.ginv;
         }
     }
+    if (HS && __syncthreads_or(ov) && threadIdx.x == 0) atomicOr(overlap + S.chain0 + I.chain, 1);
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) partials[I.slot] = tot;
 }
 
 // Persistent grid: each CTA takes items from *counter until none is left.
 // Systems must have N <= MAXT (the block size is at most MAXT).
-template <bool GRAD, int MAXT, bool PIPE>
+// HS: the hard-sphere path bias is on (hs2: squared radii per slice of every LJ
+// system, at LJSysDev::hs_off; overlap: a flag per global chain).
+template <bool GRAD, int MAXT, bool PIPE, bool HS>
 __global__ void __launch_bounds__(MAXT, 1)
     lj_paired_kernel(const LJItem* __restrict__ items, int n_items,
                      const LJSysDev<float>* __restrict__ systems, const float* __restrict__ pos,
                      float* __restrict__ grad, double* __restrict__ partials,
-                     int* __restrict__ counter, uint32_t* __restrict__ outer, long long outer_words)
+                     int* __restrict__ counter, uint32_t* __restrict__ outer, long long outer_words,
+                     const float* __restrict__ hs2, int* __restrict__ overlap)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ double red[32];
@@ -929,21 +958,31 @@ __global__ void __launch_bounds__(MAXT, 1)
         const LJItem I = items[it];
         const LJSysDev<float> S = systems[I.sys];
         if (GRAD && PIPE)
-            paired_item_pipe<MAXT>(I, S, smem_raw, pos, grad, partials, red,
-                                   outer + (long long)blockIdx.x * outer_words, &s_dmax);
+            paired_item_pipe<MAXT, HS>(I, S, smem_raw, pos, grad, partials, red,
+                                       outer + (long long)blockIdx.x * outer_words, &s_dmax, hs2,
+                                       overlap);
         else
-            paired_item<GRAD, MAXT>(I, S, smem_raw, pos, grad, partials, red,
-                                    outer + (long long)blockIdx.x * outer_words, &s_dmax);
+            paired_item<GRAD, MAXT, HS>(I, S, smem_raw, pos, grad, partials, red,
+                                        outer + (long long)blockIdx.x * outer_words, &s_dmax, hs2,
+                                        overlap);
     }
 }
 
 // The pipelined form is used with the gradient for blocks of up to 512 threads
 // (its two position buffers and staging area take 88 bytes per particle slot).
-template <bool GRAD>
+template <bool GRAD, bool HS>
 auto paired_kernel_ptr(int NT, bool pipe)
 {
-    if (GRAD && pipe && NT <= 512) return lj_paired_kernel<GRAD, 512, true>;
-    return NT <= 512 ? lj_paired_kernel<GRAD, 512, false> : lj_paired_kernel<GRAD, 1024, false>;
+    if (GRAD && pipe && NT <= 512) return lj_paired_kernel<GRAD, 512, true, HS>;
+    return NT <= 512 ? lj_paired_kernel<GRAD, 512, false, HS> : lj_paired_kernel<GRAD, 1024, false, HS>;
+}
+
+using PairedKernel = void (*)(const LJItem*, int, const LJSysDev<float>*, const float*, float*,
+                              double*, int*, uint32_t*, long long, const float*, int*);
+PairedKernel paired_kernel_sel(int NT, bool with_grad, bool pipe, bool hs)
+{
+    if (with_grad) return hs ? paired_kernel_ptr<true, true>(NT, pipe) : paired_kernel_ptr<true, false>(NT, pipe);
+    return hs ? paired_kernel_ptr<false, true>(NT, pipe) : paired_kernel_ptr<false, false>(NT, pipe);
 }
 
 }  // namespace
@@ -957,7 +996,7 @@ size_t lj_paired_smem_bytes(int NT, int cap_lane, bool pipe)
 
 int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad, bool pipe)
 {
-    auto kern = with_grad ? paired_kernel_ptr<true>(NT, pipe) : paired_kernel_ptr<false>(NT, pipe);
+    auto kern = paired_kernel_sel(NT, with_grad, pipe, false);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
@@ -969,17 +1008,17 @@ int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad, bool pipe)
 cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
                              const float* pos, float* grad, double* partials, int* counter, int NT,
                              size_t smem, int grid, bool with_grad, bool pipe, uint32_t* outer,
-                             long long outer_words, cudaStream_t st)
+                             long long outer_words, cudaStream_t st, const float* hs2, int* overlap)
 {
     if (n_items <= 0) return cudaSuccess;
     if (NT > 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    auto kern = with_grad ? paired_kernel_ptr<true>(NT, pipe) : paired_kernel_ptr<false>(NT, pipe);
+    auto kern = paired_kernel_sel(NT, with_grad, pipe, hs2 != nullptr);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, NT, smem, st>>>(items, n_items, static_cast<const LJSysDev<float>*>(sys_table),
-                                 pos, grad, partials, counter, outer, outer_words);
+                                 pos, grad, partials, counter, outer, outer_words, hs2, overlap);
     return cudaGetLastError();
 }
 

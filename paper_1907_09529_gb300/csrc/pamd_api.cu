@@ -70,6 +70,7 @@ struct SysInfo {
     int n_tiles = 0;
     long long first_slice = 0;   // time slab (0 / 0 / 0 for whole paths)
     int halo_lo = 0, halo_hi = 0;
+    long long hs_off = 0;        // LJ: first of its slices in the hard-sphere radii array
 };
 
 // Buffers and update count of a captured update graph.  Compared field by field:
@@ -145,6 +146,10 @@ struct Plan {
     uint32_t* d_outer = nullptr;
     long long outer_words = 0;  // 32-bit words per CTA region
     int n_lanes = 1;            // compute lanes of the host-buffer pipeline
+    // hard-sphere path bias (pamd_action_grad_hs): radii of every LJ slice, per-chain flags
+    long long hs_slices = 0;
+    void* d_hs2 = nullptr;
+    int* d_overlap = nullptr;
     // host-buffer pipeline: copy streams, the extra compute streams (lanes 1..), events
     // and one LJ work counter per chunk (created on first use)
     cudaStream_t s_in = nullptr, s_out = nullptr;
@@ -363,6 +368,9 @@ void fill_lj_sys(Plan* P, const pamd_problem* p)
         // results are bitwise the same, which a test checks)
         d.shared_shift = std::getenv("PAMD_LJ_PER_STEP_SHIFT") == nullptr;
         d.write_nose = !si.halo_hi;
+        d.chain0 = si.chain0;
+        d.hs_off = si.hs_off = P->hs_slices;  // this system's slices in the hard-sphere radii
+        P->hs_slices += si.T + 1;
         LJConst c;
         c.L = si.pot.box;
         c.rc = si.pot.rc;
@@ -686,7 +694,8 @@ bool is_host_ptr(const void* ptr)
 // depend on the range it is computed in.
 template <typename R>
 int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_out, bool with_grad,
-               cudaStream_t st, int c0 = 0, int c1 = -1, int* counter = nullptr, int lane = 0)
+               cudaStream_t st, int c0 = 0, int c1 = -1, int* counter = nullptr, int lane = 0,
+               const R* hs2 = nullptr, int* overlap = nullptr)
 {
     if (c1 < 0) c1 = P->n_chains;
     if (!counter) counter = P->d_counter;  // LJ work-queue counter of this launch sequence
@@ -729,9 +738,9 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
                     P->lj_NT, P->lj_smem, g, with_grad, P->lj_pipe,
                     P->d_outer + (long long)lane * std::max(P->lj_grid_grad, P->lj_grid_nograd) *
                                      P->outer_words,
-                    P->outer_words, st);
+                    P->outer_words, st, (const float*)hs2, overlap);
             return launch_lj_items<R>(items, n, P->d_lj_sys, P->lj_nmax, pos, grad, P->d_part_S,
-                                      counter, P->lj_NT, P->lj_smem, g, with_grad, st);
+                                      counter, P->lj_NT, P->lj_smem, g, with_grad, st, hs2, overlap);
         };
         if (one) {
             for (int c = c0; c < c1; ++c) {
@@ -1051,6 +1060,56 @@ static int action_common(const pamd_problem* prob, const void* pos, double* S, v
         if (dS != S)
             PAMD_CUDA_TRY(cudaMemcpyAsync(S, dS, sizeof(double) * P->n_chains, cudaMemcpyDeviceToHost, st));
         PAMD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return PAMD_OK;
+}
+
+int pamd_action_grad_hs(const pamd_problem* prob, const void* pos, const double* sigma_hs, double* S,
+                        void* grad, void* stream)
+{
+    NvtxRange nvtx_("pamd_action_grad_hs");
+    int rc = check_em_problem(prob);
+    if (rc) return rc;
+    if (!pos || !sigma_hs || !S) return PAMD_ERR_ARG;
+    for (const void* b : {pos, (const void*)sigma_hs, (const void*)S, (const void*)grad})
+        if (b && is_host_ptr(b)) return PAMD_ERR_ARG;  // device buffers only
+    std::lock_guard<std::mutex> lk(g_mutex);
+    Plan* P;
+    if ((rc = build_plan(prob, &P))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P->hs_slices > 0 && !P->d_hs2) {
+        if ((rc = P->alloc(&P->d_hs2, P->esz * (size_t)P->hs_slices))) return rc;
+        if ((rc = P->alloc(&P->d_overlap, sizeof(int) * (size_t)P->n_chains))) return rc;
+    }
+    const bool with_grad = grad != nullptr;
+    if (P->hs_slices > 0) {
+        PAMD_CUDA_TRY(cudaMemsetAsync(P->d_overlap, 0, sizeof(int) * (size_t)P->n_chains, st));
+        if (P->fp64)
+            PAMD_CUDA_TRY(launch_hs_square<double>(sigma_hs, (double*)P->d_hs2, P->hs_slices, st));
+        else
+            PAMD_CUDA_TRY(launch_hs_square<float>(sigma_hs, (float*)P->d_hs2, P->hs_slices, st));
+    }
+    if (P->fp64)
+        rc = run_action<double>(prob, P, (const double*)pos, (double*)grad, S, with_grad, st, 0, -1,
+                                nullptr, 0, (const double*)P->d_hs2, P->d_overlap);
+    else
+        rc = run_action<float>(prob, P, (const float*)pos, (float*)grad, S, with_grad, st, 0, -1,
+                               nullptr, 0, (const float*)P->d_hs2, P->d_overlap);
+    if (rc) return rc;
+    if (P->hs_slices > 0) {
+        // the last slice of every chain that owns it (the force walks stop at T-1)
+        for (const auto& si : P->sys) {
+            if (si.kind != PAMD_LJ || si.halo_hi) continue;
+            const void* row = &P->h_lj_sys[P->lj_sys_stride * si.lj_index];
+            const long long off = si.hs_off + si.T;
+            if (P->fp64)
+                PAMD_CUDA_TRY(launch_lj_hs_slice<double>((const double*)pos, row, si.chains, si.T,
+                                                         (const double*)P->d_hs2 + off, P->d_overlap, st));
+            else
+                PAMD_CUDA_TRY(launch_lj_hs_slice<float>((const float*)pos, row, si.chains, si.T,
+                                                        (const float*)P->d_hs2 + off, P->d_overlap, st));
+        }
+        PAMD_CUDA_TRY(launch_hs_fixup(S, P->d_overlap, P->n_chains, st));
     }
     return PAMD_OK;
 }

@@ -328,6 +328,8 @@ struct LJSysDev {
     int outer_cap;        // outer-list capacity per thread (paired kernel, global memory)
     int shared_shift;     // paired kernel: windows may use one image shift per list entry
     int write_nose;       // the last slice is owned (not a time-slab halo): write its gradient
+    int chain0;           // global index of chain 0
+    long long hs_off;     // hard-sphere path bias: this system's slices in the radii array
     LJK<R> k;
 };
 
@@ -347,7 +349,18 @@ int lj_blocks_per_sm(int NT, size_t smem, bool with_grad);
 template <typename R>
 cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_table, int nmax,
                             const R* pos, R* grad, double* partials, int* counter, int NT,
-                            size_t smem, int grid, bool with_grad, cudaStream_t st);
+                            size_t smem, int grid, bool with_grad, cudaStream_t st,
+                            const R* hs2 = nullptr, int* overlap = nullptr);
+
+// Hard-sphere path bias: squared radii from the caller's radii (<= 0: none, -1);
+// the all-pairs check of slice t of every chain of one system (host copy of its
+// LJSysDev row); S = +inf where a chain's overlap flag is set.
+template <typename R>
+cudaError_t launch_hs_square(const double* sigma, R* hs2, long long n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_lj_hs_slice(const R* pos, const void* sys_entry_host, int n_chains, int t,
+                               const R* hs2t, int* overlap, cudaStream_t st);
+cudaError_t launch_hs_fixup(double* S, const int* overlap, int n, cudaStream_t st);
 
 // Single-precision action (+ adjoint) with two consecutive steps per thread and
 // packed f32x2 pair arithmetic (lj_paired.cu), for systems of N <= NT <= 1024.
@@ -357,10 +370,14 @@ cudaError_t launch_lj_items(const LJItem* items, int n_items, const void* sys_ta
 size_t lj_paired_smem_bytes(int NT, int cap_lane, bool pipe);
 int lj_paired_blocks_per_sm(int NT, size_t smem, bool with_grad, bool pipe);
 // outer: per-CTA outer lists, outer_words 32-bit words for each of grid CTAs.
+// hs2 (NULL: no bias): squared hard-sphere radii per slice of every LJ system
+// (LJSysDev::hs_off); overlap: per global chain, set to 1 where a pair lies within
+// its slice's radius at a slice whose force the launch evaluates.
 cudaError_t launch_lj_paired(const LJItem* items, int n_items, const void* sys_table,
                              const float* pos, float* grad, double* partials, int* counter, int NT,
                              size_t smem, int grid, bool with_grad, bool pipe, uint32_t* outer,
-                             long long outer_words, cudaStream_t st);
+                             long long outer_words, cudaStream_t st, const float* hs2 = nullptr,
+                             int* overlap = nullptr);
 
 cudaError_t launch_lj_pair_counts(const float* pos, long long* counts, int N, int T, int n_chains,
                                   long long sys_offset, double L, double rc, cudaStream_t st);

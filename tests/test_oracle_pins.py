@@ -536,3 +536,83 @@ def test_shift_regenerate_grows_free_particle_walks():
     sd = np.sqrt(np.diag(cov))
     assert np.all(np.abs(nose.mean(0) - pos[T, 0, 0]) < 5 * sd / math.sqrt(n))
     assert np.all(np.abs(np.cov(nose, rowvar=False) - cov) < 6 * np.outer(sd, sd) * math.sqrt(2.0 / n))
+
+
+def _hs_path(T, box, d_pair, t_pair, rng_seed=3):
+    """Four particles far apart in a box of side `box`, except that particles 0
+    and 1 sit exactly d_pair apart along x at slice t_pair (elsewhere 2.0 apart);
+    particle 3 sits across the periodic boundary from particle 2 (min image 1.6)."""
+    g = inputs.rng(rng_seed)
+    pos = np.zeros((T + 1, 3, 4))
+    for t in range(T + 1):
+        c = np.array([4.0, 4.0, 4.0]) + 1e-3 * g.standard_normal(3)
+        sep = d_pair if t == t_pair else 2.0
+        pos[t, :, 0] = c
+        pos[t, :, 1] = c + np.array([sep, 0.0, 0.0])
+        pos[t, :, 2] = [0.3, 8.5, 8.5]
+        pos[t, :, 3] = [box - 1.3, 8.5, 8.5]   # 1.6 from particle 2 through the face
+    return pos
+
+
+def test_hard_sphere_bias_closed_forms():
+    """The hard-sphere path bias (Sec. IV.B): infinite exactly when a pair within
+    the cutoff is at r <= sigma_HS(t) at some slice, the plain LJ action (bit for
+    bit) otherwise; minimum image; sigma_HS above rc acts as rc."""
+    T, box, rc = 6, 12.0, 2.5
+    pot = oracle.lennard_jones(box, rc)
+    D, beta, dt = 1.0, 1.0, 1e-3
+    pos = _hs_path(T, box, 0.95, 4)
+    S_lj, g_lj = oracle.action_grad(pot, pos, D, beta, dt)
+    zero = np.zeros(T + 1)
+    assert oracle.hs_first_overlap(pot, pos, zero) == -1
+    S, g = oracle.action_grad_hs(pot, pos, zero, D, beta, dt)
+    assert S == S_lj and np.array_equal(g, g_lj)
+    # the pair 0.95 apart at slice 4: caught by sigma 0.96 at that slice only
+    sig = zero.copy()
+    sig[4] = 0.96
+    assert oracle.hs_first_overlap(pot, pos, sig) == 4
+    S, g = oracle.action_grad_hs(pot, pos, sig, D, beta, dt)
+    assert S == math.inf and np.array_equal(g, g_lj)
+    sig[4] = 0.94
+    assert oracle.hs_first_overlap(pot, pos, sig) == -1
+    assert oracle.action_grad_hs(pot, pos, sig, D, beta, dt)[0] == S_lj
+    # sigma 1.9 everywhere: the 2.0 pairs pass, the 1.6 pair through the face overlaps
+    sig = np.full(T + 1, 1.9)
+    sig[4] = 0.0
+    assert oracle.hs_first_overlap(pot, pos, sig) == 0
+    # sigma 1.9 only at the nose: still caught there (every slice counts, x_T too)
+    sig = zero.copy()
+    sig[T] = 1.9
+    assert oracle.hs_first_overlap(pot, pos, sig) == T
+    # sigma above rc acts as rc: the 2.0 pairs (inside rc) overlap, nothing beyond rc does
+    far = pos.copy()
+    far[:, :, 3] = [6.0, 1.0, 1.0]                 # the face pair moved out of range
+    sig = zero.copy()
+    sig[2] = 3.0
+    assert oracle.hs_first_overlap(pot, far, sig) == 2
+    far[:, 0, 1] = far[:, 0, 0] + 2.6              # pair 0-1 beyond rc = 2.5
+    assert oracle.hs_first_overlap(pot, far, sig) == -1
+
+
+def test_hard_sphere_overlap_f32_agrees_away_from_the_threshold():
+    """The single-precision mirror of the overlap decision equals the exact one
+    whenever no pair distance is within 1e-4 of sigma."""
+    box, rc = 6.0, 2.5
+    pot = oracle.lennard_jones(box, rc)
+    g = inputs.rng(11)
+    checked = 0
+    for trial in range(40):
+        x = g.uniform(0, box, size=(3, 16))
+        dmin = np.inf
+        for i in range(16):
+            for j in range(i + 1, 16):
+                dv = x[:, i] - x[:, j]
+                dv -= box * np.round(dv / box)
+                dmin = min(dmin, float(np.linalg.norm(dv)))
+        for sigma in (0.5, 0.8, 1.0, 1.2):
+            if abs(dmin - sigma) < 1e-4:
+                continue
+            exact = oracle.hs_first_overlap(pot, x[None], [sigma]) == 0
+            assert oracle.hs_overlap_f32(box, rc, sigma, x.astype(np.float32)) == exact
+            checked += 1
+    assert checked > 100
