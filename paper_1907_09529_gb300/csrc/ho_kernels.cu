@@ -15,7 +15,9 @@
 
 namespace pamd {
 
-template <typename R, bool GRAD>
+// SLAB: the blocks belong to a time slab (owned elements and the summed steps
+// masked); whole paths take the form without the masks.
+template <typename R, bool GRAD, bool SLAB>
 __global__ void __launch_bounds__(kElemThreads)
     ho_action_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
                      R* __restrict__ grad, double* __restrict__ partials, int slot0, R a, R ginv)
@@ -47,9 +49,9 @@ __global__ void __launch_bounds__(kElemThreads)
         const R xm = xs[q], x0 = xs[q + s], xp = xs[q + 2 * s];
         const R rp = (e >= s) ? fma_r(ak, xm, x0 - xm) : R(0);
         const R r = (e < rend) ? fma_r(ak, x0, xp - x0) : R(0);
-        if (GRAD && e >= B.own_lo && e < B.own_hi && PAMD_OK_IDX(e, B.chain_len))
+        if (GRAD && (!SLAB || (e >= B.own_lo && e < B.own_hi)) && PAMD_OK_IDX(e, B.chain_len))
             grad[B.chain_base + e] = fma_r(ak, r, rp - r) * ginv;
-        if (e >= B.sum_lo) acc = fma_r(r, r, acc);
+        if (!SLAB || e >= B.sum_lo) acc = fma_r(r, r, acc);
     }
     const double tot = block_sum((double)acc, red);
     if (threadIdx.x == 0) partials[slot0 + blockIdx.x] = tot;
@@ -58,28 +60,21 @@ __global__ void __launch_bounds__(kElemThreads)
 template <typename R>
 cudaError_t launch_ho_action(const ElemBlock* blocks, int n_blocks, int max_s, const R* pos, R* grad,
                              double* partials, int slot0, double a, double ginv, bool with_grad,
-                             cudaStream_t st)
+                             cudaStream_t st, bool slab)
 {
     if (n_blocks <= 0) return cudaSuccess;
     const size_t smem = sizeof(R) * (size_t)(kElemChunk + 2 * max_s);
-    if (with_grad) {
-        auto k = ho_action_kernel<R, true>;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<n_blocks, kElemThreads, smem, st>>>(blocks, pos, grad, partials, slot0, (R)a, (R)ginv);
-    } else {
-        auto k = ho_action_kernel<R, false>;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<n_blocks, kElemThreads, smem, st>>>(blocks, pos, grad, partials, slot0, (R)a, (R)ginv);
-    }
+    auto k = with_grad ? (slab ? ho_action_kernel<R, true, true> : ho_action_kernel<R, true, false>)
+                       : (slab ? ho_action_kernel<R, false, true> : ho_action_kernel<R, false, false>);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<n_blocks, kElemThreads, smem, st>>>(blocks, pos, grad, partials, slot0, (R)a, (R)ginv);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_ho_action<float>(const ElemBlock*, int, int, const float*, float*,
-                                             double*, int, double, double, bool, cudaStream_t);
+                                             double*, int, double, double, bool, cudaStream_t, bool);
 template cudaError_t launch_ho_action<double>(const ElemBlock*, int, int, const double*, double*,
-                                              double*, int, double, double, bool, cudaStream_t);
+                                              double*, int, double, double, bool, cudaStream_t, bool);
 
 // ------------------------------------------------------------------ vectorised form (s <= 4)
 // When a slice holds at most 4 elements (one particle in 1-3D, or a few in 1D),
@@ -89,7 +84,7 @@ template cudaError_t launch_ho_action<double>(const ElemBlock*, int, int, const 
 // registers and stores one float4: no shared-memory staging and no barrier
 // before the final block sum.  The unaligned ends of a block (< 4 elements
 // each) are done element by element.
-template <int S, bool GRAD>
+template <int S, bool GRAD, bool SLAB>
 __global__ void __launch_bounds__(kElemThreads)
     ho_vec_kernel(const ElemBlock* __restrict__ blocks, const float* __restrict__ pos,
                   float* __restrict__ grad, double* __restrict__ partials, int slot0, float a,
@@ -119,10 +114,10 @@ __global__ void __launch_bounds__(kElemThreads)
             const float rp = (le >= S) ? fma_r(ak, xm, x0 - xm) : 0.f;
             const float r = (le < rend) ? fma_r(ak, x0, xp - x0) : 0.f;
             out[l] = fma_r(ak, r, rp - r) * ginv;
-            if (le >= B.sum_lo) acc = fma_r(r, r, acc);
+            if (!SLAB || le >= B.sum_lo) acc = fma_r(r, r, acc);
         }
         if (GRAD) {
-            if (le0 >= B.own_lo && le0 + 3 < B.own_hi) {
+            if (!SLAB || (le0 >= B.own_lo && le0 + 3 < B.own_hi)) {
                 *reinterpret_cast<float4*>(grad + g) = make_float4(out[0], out[1], out[2], out[3]);
             } else {  // a vector holding time-slab halo elements
 #pragma unroll
@@ -145,8 +140,8 @@ __global__ void __launch_bounds__(kElemThreads)
         const float xp = (le < rend && ok) ? pos[g + S] : 0.f;
         const float rp = (le >= S) ? fma_r(ak, xm, x0 - xm) : 0.f;
         const float r = (le < rend) ? fma_r(ak, x0, xp - x0) : 0.f;
-        if (GRAD && le >= B.own_lo && le < B.own_hi && ok) grad[g] = fma_r(ak, r, rp - r) * ginv;
-        if (le >= B.sum_lo) acc = fma_r(r, r, acc);
+        if (GRAD && (!SLAB || (le >= B.own_lo && le < B.own_hi)) && ok) grad[g] = fma_r(ak, r, rp - r) * ginv;
+        if (!SLAB || le >= B.sum_lo) acc = fma_r(r, r, acc);
     }
     const double tot = block_sum((double)acc, red);
     if (threadIdx.x == 0) partials[slot0 + blockIdx.x] = tot;
@@ -155,9 +150,10 @@ __global__ void __launch_bounds__(kElemThreads)
 template <int S>
 static cudaError_t launch_vec_s(const ElemBlock* blocks, int n_blocks, const float* pos, float* grad,
                                 double* partials, int slot0, double a, double ginv, bool with_grad,
-                                long long sys_lo, long long sys_hi, cudaStream_t st)
+                                long long sys_lo, long long sys_hi, cudaStream_t st, bool slab)
 {
-    auto kern = with_grad ? ho_vec_kernel<S, true> : ho_vec_kernel<S, false>;
+    auto kern = with_grad ? (slab ? ho_vec_kernel<S, true, true> : ho_vec_kernel<S, true, false>)
+                          : (slab ? ho_vec_kernel<S, false, true> : ho_vec_kernel<S, false, false>);
     kern<<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, grad, partials, slot0, (float)a, (float)ginv,
                                             sys_lo, sys_hi);
     return cudaGetLastError();
@@ -165,14 +161,15 @@ static cudaError_t launch_vec_s(const ElemBlock* blocks, int n_blocks, const flo
 
 cudaError_t launch_ho_action_vec(const ElemBlock* blocks, int n_blocks, int s, const float* pos,
                                  float* grad, double* partials, int slot0, double a, double ginv,
-                                 bool with_grad, long long sys_lo, long long sys_hi, cudaStream_t st)
+                                 bool with_grad, long long sys_lo, long long sys_hi, cudaStream_t st,
+                                 bool slab)
 {
     if (n_blocks <= 0) return cudaSuccess;
     switch (s) {
-        case 1: return launch_vec_s<1>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
-        case 2: return launch_vec_s<2>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
-        case 3: return launch_vec_s<3>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
-        case 4: return launch_vec_s<4>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st);
+        case 1: return launch_vec_s<1>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st, slab);
+        case 2: return launch_vec_s<2>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st, slab);
+        case 3: return launch_vec_s<3>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st, slab);
+        case 4: return launch_vec_s<4>(blocks, n_blocks, pos, grad, partials, slot0, a, ginv, with_grad, sys_lo, sys_hi, st, slab);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -149,6 +149,7 @@ struct Plan {
     // hard-sphere path bias (pamd_action_grad_hs): radii of every LJ slice, per-chain flags
     long long hs_slices = 0;
     void* d_hs2 = nullptr;
+    bool any_slab = false;      // some system is a time slab
     int* d_overlap = nullptr;
     // host-buffer pipeline: copy streams, the extra compute streams (lanes 1..), events
     // and one LJ work counter per chunk (created on first use)
@@ -429,6 +430,7 @@ int build_plan(const pamd_problem* p, Plan** out)
         si.first_slice = s.first_slice;
         si.halo_lo = s.halo_lo;
         si.halo_hi = s.halo_hi;
+        P->any_slab = P->any_slab || s.first_slice || s.halo_lo || s.halo_hi;
         P->span = std::max(P->span, si.off + si.chain_len * si.chains);
         P->sys.push_back(si);
         chain += s.n_chains;
@@ -709,14 +711,15 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
         if (lo_c >= hi_c) continue;
         const int sz = si.d * si.N;
         const long long lo = si.off, hi = si.off + si.chain_len * si.chains;
+        const bool slab = si.halo_lo || si.halo_hi;
         auto ho = [&](int b0, int nb) -> int {
             if (std::is_same<R, float>::value && sz <= 4)
                 PAMD_CUDA_TRY(launch_ho_action_vec(P->d_ho + b0, nb, sz, (const float*)pos,
                                                    (float*)grad, P->d_part_S, b0, a, ginv, with_grad,
-                                                   lo, hi, st));
+                                                   lo, hi, st, slab));
             else
                 PAMD_CUDA_TRY(launch_ho_action<R>(P->d_ho + b0, nb, P->max_s_ho, pos, grad, P->d_part_S,
-                                                  b0, a, ginv, with_grad, st));
+                                                  b0, a, ginv, with_grad, st, slab));
             return PAMD_OK;
         };
         int rc;
@@ -774,11 +777,11 @@ int run_one_update(const pamd_problem* p, Plan* P, R* pos, R* grad, double* S, c
     R* prop = reinterpret_cast<R*>(P->d_prop);
     R* gprop = reinterpret_cast<R*>(P->d_gprop);
     PAMD_CUDA_TRY(launch_mala_propose<R>(P->d_all + eb0, eb1 - eb0, pos, grad, noise, prop,
-                                         P->d_part_qf + eb0, P->d_md, u, st));
+                                         P->d_part_qf + eb0, P->d_md, u, st, P->any_slab));
     int rc = run_action<R>(p, P, prop, gprop, P->d_Sprop, true, st, c0, c1, counter, lane);
     if (rc) return rc;
     PAMD_CUDA_TRY(launch_mala_reverse<R>(P->d_all + eb0, eb1 - eb0, pos, prop, gprop,
-                                         P->d_part_qr + eb0, P->d_md, st));
+                                         P->d_part_qr + eb0, P->d_md, st, P->any_slab));
     PAMD_CUDA_TRY(launch_finalize(P->d_part_qf, P->d_E_slots + c0, c1 - c0, 1.0, P->d_qf + c0, st));
     PAMD_CUDA_TRY(launch_finalize(P->d_part_qr, P->d_E_slots + c0, c1 - c0, 1.0, P->d_qr + c0, st));
     PAMD_CUDA_TRY(launch_mala_accept(c0, c1 - c0, S, P->d_Sprop, P->d_qf, P->d_qr, log_u, P->d_md, u,
@@ -1277,11 +1280,11 @@ int pamd_mala_propose(const pamd_problem* prob, const void* pos, const void* gra
     if (P->fp64)
         PAMD_CUDA_TRY(launch_mala_propose<double>(P->d_all, nb, (const double*)pos, (const double*)grad,
                                                   (const double*)noise, (double*)prop, P->d_part_qf,
-                                                  P->d_md, 0, st));
+                                                  P->d_md, 0, st, P->any_slab));
     else
         PAMD_CUDA_TRY(launch_mala_propose<float>(P->d_all, nb, (const float*)pos, (const float*)grad,
                                                  (const float*)noise, (float*)prop, P->d_part_qf,
-                                                 P->d_md, 0, st));
+                                                 P->d_md, 0, st, P->any_slab));
     PAMD_CUDA_TRY(launch_finalize(P->d_part_qf, P->d_E_slots, P->n_chains, 1.0, q_fwd, st));
     return PAMD_OK;
 }
@@ -1300,10 +1303,12 @@ int pamd_mala_reverse(const pamd_problem* prob, const void* pos, const void* pro
     PAMD_CUDA_TRY(launch_set_mala_params(P->d_md, 0, 0, h, st));
     if (P->fp64)
         PAMD_CUDA_TRY(launch_mala_reverse<double>(P->d_all, nb, (const double*)pos, (const double*)prop,
-                                                  (const double*)grad_prop, P->d_part_qr, P->d_md, st));
+                                                  (const double*)grad_prop, P->d_part_qr, P->d_md, st,
+                                                  P->any_slab));
     else
         PAMD_CUDA_TRY(launch_mala_reverse<float>(P->d_all, nb, (const float*)pos, (const float*)prop,
-                                                 (const float*)grad_prop, P->d_part_qr, P->d_md, st));
+                                                 (const float*)grad_prop, P->d_part_qr, P->d_md, st,
+                                                 P->any_slab));
     PAMD_CUDA_TRY(launch_finalize(P->d_part_qr, P->d_E_slots, P->n_chains, 1.0, q_rev, st));
     return PAMD_OK;
 }

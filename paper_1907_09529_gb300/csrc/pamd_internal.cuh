@@ -245,17 +245,20 @@ struct ChainSlots {
 // ------------------------------------------------------------------ launchers
 // Harmonic action (+ gradient) over element blocks.  Writes one partial
 // sum of |r|^2 per block into partials[slot0 + block].
+// slab: the blocks belong to a time slab (ElemBlock's owned range and summed
+// steps applied); false for whole paths.
 template <typename R>
 cudaError_t launch_ho_action(const ElemBlock* blocks, int n_blocks, int max_s, const R* pos, R* grad,
                              double* partials, int slot0, double a, double ginv, bool with_grad,
-                             cudaStream_t st);
+                             cudaStream_t st, bool slab);
 
 // Single-precision form for slices of s <= 4 elements: aligned float4 loads and
 // stores, neighbours from registers.  The blocks must all belong to one system
 // whose elements span [sys_lo, sys_hi) of the buffer (reads stay inside it).
 cudaError_t launch_ho_action_vec(const ElemBlock* blocks, int n_blocks, int s, const float* pos,
                                  float* grad, double* partials, int slot0, double a, double ginv,
-                                 bool with_grad, long long sys_lo, long long sys_hi, cudaStream_t st);
+                                 bool with_grad, long long sys_lo, long long sys_hi, cudaStream_t st,
+                                 bool slab);
 
 struct LJConst {
     double L, rc, eps, sigma, a, ginv, skin;
@@ -406,14 +409,16 @@ struct MalaDev {
     uint64_t counter;
     double h;
 };
+// slab: some block belongs to a time slab (halo elements copied / skipped, noise
+// indexed from the whole path's slice 0); false for whole paths.
 template <typename R>
 cudaError_t launch_mala_propose(const ElemBlock* blocks, int n_blocks, const R* pos, const R* grad,
                                 const R* noise, R* prop, double* part_qf, const MalaDev* md,
-                                int update_index, cudaStream_t st);
+                                int update_index, cudaStream_t st, bool slab);
 template <typename R>
 cudaError_t launch_mala_reverse(const ElemBlock* blocks, int n_blocks, const R* pos, const R* prop,
                                 const R* grad_prop, double* part_qr, const MalaDev* md,
-                                cudaStream_t st);
+                                cudaStream_t st, bool slab);
 // Accept test for chains [chain0, chain0 + n_chains) (arrays indexed by global chain).
 cudaError_t launch_mala_accept(int chain0, int n_chains, const double* S, const double* S_prop,
                                const double* qf, const double* qr, const double* log_u,

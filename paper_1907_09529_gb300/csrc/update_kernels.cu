@@ -70,7 +70,7 @@ cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter,
 // element e is component (g & 3) of the Philox call for group g >> 2, g = e_glob + e
 // its whole-path index (one call per group on whole paths).  Elements outside
 // [s, own_hi) -- the fixed tail x_0 or a time slab's halo slices -- are copied.
-template <typename R>
+template <typename R, bool SLAB>
 __global__ void __launch_bounds__(kElemThreads)
     mala_propose_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
                         const R* __restrict__ grad, const R* __restrict__ noise, R* __restrict__ prop,
@@ -86,22 +86,28 @@ __global__ void __launch_bounds__(kElemThreads)
     const int ng = (B.n + 3) >> 2;             // e0 is a multiple of 4
     for (int gq = threadIdx.x; gq < ng; gq += kElemThreads) {
         float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        long long zg = -1;                     // Philox group held in z4
+        long long zg = -1;                     // Philox group held in z4 (time slabs)
+        if (!SLAB && !noise)                   // whole paths: the group of the 4 elements
+            z4 = philox_normals4(seed, counter, kStreamMala, (uint32_t)B.chain,
+                                 (uint32_t)((B.e0 >> 2) + gq));
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             const int e = B.e0 + 4 * gq + l;
             if (e >= B.e0 + B.n) break;
             if (!PAMD_OK_IDX(e, B.chain_len)) continue;
             const R x = pos[base + e];
-            if (e < B.s || e >= B.own_hi) {  // fixed tail x_0, or a time-slab halo
+            if (e < B.s || (SLAB && e >= B.own_hi)) {  // fixed tail x_0, or a time-slab halo
                 prop[base + e] = x;
                 continue;
             }
             const R g = grad[base + e];
-            const long long ge = B.e_glob + e;
-            if (!noise && (ge >> 2) != zg) {
-                zg = ge >> 2;
-                z4 = philox_normals4(seed, counter, kStreamMala, (uint32_t)B.chain, (uint32_t)zg);
+            long long ge = e;
+            if (SLAB) {
+                ge = B.e_glob + e;
+                if (!noise && (ge >> 2) != zg) {
+                    zg = ge >> 2;
+                    z4 = philox_normals4(seed, counter, kStreamMala, (uint32_t)B.chain, (uint32_t)zg);
+                }
             }
             const R z = noise ? noise[base + e] : (R)pick4(z4, (int)(ge & 3));
             const R xp = x + fma_r(-h, g, s2h * z);
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(kElemThreads)
     if (threadIdx.x == 0) part_qf[blockIdx.x] = tot;
 }
 
-template <typename R>
+template <typename R, bool SLAB>
 __global__ void __launch_bounds__(kElemThreads)
     mala_reverse_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
                         const R* __restrict__ prop, const R* __restrict__ grad_prop,
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(kElemThreads)
 #pragma unroll 4
     for (int q = threadIdx.x; q < B.n; q += kElemThreads) {
         const int e = B.e0 + q;
-        if (e < B.s || e >= B.own_hi || !PAMD_OK_IDX(e, B.chain_len)) continue;
+        if (e < B.s || (SLAB && e >= B.own_hi) || !PAMD_OK_IDX(e, B.chain_len)) continue;
         const R x = pos[base + e], xp = prop[base + e], gp = grad_prop[base + e];
         const R b = fma_r(h, gp, x - xp);
         acc = fma_r(b, b, acc);
@@ -186,21 +192,22 @@ __global__ void __launch_bounds__(kElemThreads)
 template <typename R>
 cudaError_t launch_mala_propose(const ElemBlock* blocks, int n_blocks, const R* pos, const R* grad,
                                 const R* noise, R* prop, double* part_qf, const MalaDev* md,
-                                int update_index, cudaStream_t st)
+                                int update_index, cudaStream_t st, bool slab)
 {
     if (n_blocks <= 0) return cudaSuccess;
-    mala_propose_kernel<R><<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, grad, noise, prop, part_qf,
-                                                              md, update_index);
+    auto k = slab ? mala_propose_kernel<R, true> : mala_propose_kernel<R, false>;
+    k<<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, grad, noise, prop, part_qf, md, update_index);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_mala_reverse(const ElemBlock* blocks, int n_blocks, const R* pos, const R* prop,
                                 const R* grad_prop, double* part_qr, const MalaDev* md,
-                                cudaStream_t st)
+                                cudaStream_t st, bool slab)
 {
     if (n_blocks <= 0) return cudaSuccess;
-    mala_reverse_kernel<R><<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, prop, grad_prop, part_qr, md);
+    auto k = slab ? mala_reverse_kernel<R, true> : mala_reverse_kernel<R, false>;
+    k<<<n_blocks, kElemThreads, 0, st>>>(blocks, pos, prop, grad_prop, part_qr, md);
     return cudaGetLastError();
 }
 
@@ -231,9 +238,10 @@ cudaError_t launch_mala_commit(const ElemBlock* blocks, int n_blocks, R* pos, R*
 #define PAMD_INST(R)                                                                               \
     template cudaError_t launch_mala_propose<R>(const ElemBlock*, int, const R*, const R*,         \
                                                 const R*, R*, double*, const MalaDev*, int,        \
-                                                cudaStream_t);                                     \
+                                                cudaStream_t, bool);                               \
     template cudaError_t launch_mala_reverse<R>(const ElemBlock*, int, const R*, const R*,         \
-                                                const R*, double*, const MalaDev*, cudaStream_t);  \
+                                                const R*, double*, const MalaDev*, cudaStream_t,   \
+                                                bool);                                             \
     template cudaError_t launch_mala_commit<R>(const ElemBlock*, int, R*, R*, const R*, const R*,  \
                                                const int*, double*, const double*, cudaStream_t);
 PAMD_INST(float)
