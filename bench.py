@@ -524,6 +524,7 @@ def main():
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
+    n_acc_steps = float(nacc.sum().item())  # accepted proposals of the warm-up and timed steps
     ms_max = max_over_ranks(ms, dev)
     value = aggregate(units_rank, world, args.steps, ms_max)
 
@@ -689,7 +690,7 @@ def main():
                        "lj_launch_shape": tuned or "default"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "plain_fp64": plain,
             "gpu_launches": args.steps * (launches_per_update(prob)) + 1 * args.steps,
-            "clocks": clk, "graph_loop": graph_loop, "accept_rate": float(nacc.sum().item()) / max(
+            "clocks": clk, "graph_loop": graph_loop, "accept_rate": n_acc_steps / max(
                 1, prob.n_chains * (args.steps + args.warmup)),
         }
         print(json.dumps(out), flush=True)

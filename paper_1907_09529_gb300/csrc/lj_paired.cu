@@ -40,10 +40,16 @@
 // slice), which holds every pair that any of the item's windows can need; it
 // sits in global memory (one region per CTA, L2-resident).  A particle whose
 // outer list overflows builds its window lists from all candidates; one whose
-// window list overflows scans all candidates.  Candidates are visited in
-// increasing j in every case, so each force and Hessian sum runs over the
-// in-cutoff pairs in one fixed order whatever the tiling, window or list
-// capacity, and the results are bitwise independent of them.
+// window list overflows scans all candidates.  Candidates are visited in one
+// fixed order in every case -- by class (j - tid) mod 8, then by increasing j --
+// so each force and Hessian sum runs over the in-cutoff pairs in one order
+// whatever the tiling, window or list capacity, and the results are bitwise
+// independent of them.  The class order spreads a warp's gathers over the
+// shared-memory banks: at the start of a walk the eight lanes of a quarter warp
+// read particles j of eight different residues mod 8, i.e. eight different
+// 16-byte bank groups, and they drift apart only as their classes run out.
+#include <type_traits>
+
 #include "pamd_internal.cuh"
 
 namespace pamd {
@@ -106,9 +112,10 @@ struct Smem {
 //   [0, 32 NMAX)        xy of buffers 0 and 1
 //   [32 NMAX, 48 NMAX)  rxy
 //   [48 NMAX, 64 NMAX)  staged references {x, y, z, delta}
-//   [64 NMAX, 80 NMAX)  z of buffers 0 and 1
+//   [64 NMAX, 80 NMAX)  zz[j] = {z_a, z_b} of buffer 0, then of buffer 1
 //   [80 NMAX, 88 NMAX)  rz
 //   [88 NMAX, ...)      neighbour lists
+// A walk that uses both buffers reads both z pairs with one 16-byte load.
 template <int NMAX>
 struct SmemP {
     unsigned char* base;
@@ -118,8 +125,9 @@ struct SmemP {
     }
     __device__ float2& z(int buf, int o8) const
     {
-        return PAMD_SLOT(float2, base + 64 * NMAX + 8 * NMAX * buf + o8, o8);
+        return PAMD_SLOT(float2, base + 64 * NMAX + 2 * o8 + 8 * buf, o8);
     }
+    __device__ float4& zz(int o8) const { return PAMD_SLOT(float4, base + 64 * NMAX + 2 * o8, o8); }
     __device__ float4& rxy(int o8) const { return PAMD_SLOT(float4, base + 32 * NMAX + 2 * o8, o8); }
     __device__ float2& rz(int o8) const { return PAMD_SLOT(float2, base + 80 * NMAX + o8, o8); }
     __device__ float4& ref(int o8) const { return PAMD_SLOT(float4, base + 48 * NMAX + 2 * o8, o8); }
@@ -288,6 +296,24 @@ struct PairList {
         ovf = false;
     }
 
+    // Candidate order.  This thread's candidates are j = q (mod tpp); they are
+    // visited class by class, class c holding j = tid + c (mod 8) for c = 0,
+    // cstep(), ... < 8, each class in increasing j (stride cls_stride()).  For
+    // tpp >= 8 all of them lie in class 0 (j = q = tid mod 8).
+    __device__ __forceinline__ int cstep() const { return tpp < 8 ? tpp : 8; }
+    __device__ __forceinline__ int cls_stride() const { return tpp < 8 ? 8 : tpp; }
+    __device__ __forceinline__ int cls_first(int c) const { return tpp < 8 ? ((tid + c) & 7) : q; }
+
+    // Calls f(j1, j2) over this thread's candidates in order, two at a time within
+    // a class (j2 = j1 + cls_stride(), possibly >= N).
+    template <typename F>
+    __device__ __forceinline__ void candidate_pairs(F&& f) const
+    {
+        const int st = cls_stride();
+        for (int c = 0; c < 8; c += cstep())
+            for (int j = cls_first(c); j < N; j += 2 * st) f(j, j + st);
+    }
+
     // Entry c of this thread is half (c & 1) of word (c >> 1) * NT + tid.
     __device__ __forceinline__ void put(int c, int o8) const
     {
@@ -316,7 +342,7 @@ struct PairList {
     }
 
     // Outer list of the item (reference and item-wide margins staged): all
-    // candidates j = q (mod tpp), in increasing j.
+    // candidates, in the candidate order.
     template <class SM>
     __device__ void build_outer(const SM& P, const K2& k)
     {
@@ -332,20 +358,19 @@ struct PairList {
                 ++c;
             }
         };
-        for (int j = q; j < N; j += 2 * tpp) {
-            const int j2 = j + tpp;
+        candidate_pairs([&](int j, int j2) {
             const int j2c = j2 < N ? j2 : j;
             bool in1, in2;
             test2(P, k, pi, 8 * j, 8 * j2c, in1, in2);
             add(j != i && in1, 8 * j);
             add(j2 < N && j2 != i && in2, 8 * j2);
-        }
+        });
         ocnt = c;
         oovf = c > ocap;
     }
 
     // Window list (window reference and margins staged) from the outer list,
-    // or from all candidates if the outer list overflowed; increasing j.
+    // or from all candidates if the outer list overflowed; candidate order.
     template <class SM>
     __device__ void build(const SM& P, const K2& k)
     {
@@ -373,20 +398,19 @@ struct PairList {
                 add(two && in2, o2);
             }
         } else {
-            for (int j = q; j < N; j += 2 * tpp) {
-                const int j2 = j + tpp;
+            candidate_pairs([&](int j, int j2) {
                 const int j2c = j2 < N ? j2 : j;
                 bool in1, in2;
                 test2(P, k, pi, 8 * j, 8 * j2c, in1, in2);
                 add(j != i && in1, 8 * j);
                 add(j2 < N && j2 != i && in2, 8 * j2);
-            }
+            });
         }
         cnt = c;
         ovf = c > cap;
     }
 
-    // Calls f(8 j) for the candidates j of particle i, in increasing j.
+    // Calls f(8 j) for the candidates j of particle i, in the candidate order.
     template <typename F>
     __device__ __forceinline__ void for_each_candidate(F&& f) const
     {
@@ -401,8 +425,10 @@ struct PairList {
             }
             if (m < cnt) f((int)((PAMD_OK_IDX((m >> 1) * NT + tid, (cap >> 1) * NT) ? *w : 0u) & 0xFFFFu));
         } else {
-            for (int j = q; j < N; j += tpp)
-                if (j != i) f(8 * j);
+            const int st = cls_stride();
+            for (int c = 0; c < 8; c += cstep())
+                for (int j = cls_first(c); j < N; j += st)
+                    if (j != i) f(8 * j);
         }
     }
 
@@ -472,27 +498,36 @@ struct PairList {
     // reference, so the shift is the nearest image's at each of them).
     // HS: also raise `ov` when a pair of the force walk lies within the hard-sphere
     // radii (squared: hs2 for the force pair's two steps) of the path bias.
-    template <bool DO_H, bool DO_F, bool SK, bool HS = false>
-    __device__ void combined(const SmemP<NMAX>& P, int hb, int fb, float2 vix, float2 viy,
-                             float2 viz, const K2& k, float2& hx, float2& hy, float2& hz,
-                             float2& fx, float2& fy, float2& fz, float2 hs2 = float2(),
-                             bool* ov = nullptr) const
+    // HB, FB: the position buffers of the Hessian-vector and force pairs.
+    template <bool DO_H, bool DO_F, bool SK, bool HS, int HB, int FB>
+    __device__ void combined(const SmemP<NMAX>& P, float2 vix, float2 viy, float2 viz, const K2& k,
+                             float2& hx, float2& hy, float2& hz, float2& fx, float2& fy, float2& fz,
+                             float2 hs2 = float2(), bool* ov = nullptr) const
     {
         hx = hy = hz = fx = fy = fz = pk(0.0f);
         if (active) {
             bool o = false;
-            const float4 hxy = P.xy(hb, 8 * i);
-            const float2 hxi = pk(hxy.x, hxy.y), hyi = pk(hxy.z, hxy.w), hzi = P.z(hb, 8 * i);
-            const float4 fxy = P.xy(fb, 8 * i);
-            const float2 fxi = pk(fxy.x, fxy.y), fyi = pk(fxy.z, fxy.w), fzi = P.z(fb, 8 * i);
+            const float4 hxy = P.xy(HB, 8 * i);
+            const float2 hxi = pk(hxy.x, hxy.y), hyi = pk(hxy.z, hxy.w), hzi = P.z(HB, 8 * i);
+            const float4 fxy = P.xy(FB, 8 * i);
+            const float2 fxi = pk(fxy.x, fxy.y), fyi = pk(fxy.z, fxy.w), fzi = P.z(FB, 8 * i);
             for_each_candidate([&](int o8) {
                 float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+                float2 hzj, fzj;  // z of particle j in the two buffers
+                if (DO_H && DO_F && HB != FB) {
+                    const float4 zz = P.zz(o8);
+                    hzj = HB ? pk(zz.z, zz.w) : pk(zz.x, zz.y);
+                    fzj = FB ? pk(zz.z, zz.w) : pk(zz.x, zz.y);
+                } else {
+                    if (DO_H) hzj = P.z(HB, o8);
+                    if (DO_F) fzj = P.z(FB, o8);
+                }
                 if (DO_H) {
                     float2 dx, dy, dz, ri, ir2, ir6, ir8;
                     if (SK)
-                        pair_vec_shift(hxi, hyi, hzi, P.xy(hb, o8), P.z(hb, o8), k, dx, dy, dz, sx, sy, sz);
+                        pair_vec_shift(hxi, hyi, hzi, P.xy(HB, o8), hzj, k, dx, dy, dz, sx, sy, sz);
                     else
-                        pair_vec(hxi, hyi, hzi, P.xy(hb, o8), P.z(hb, o8), k, dx, dy, dz);
+                        pair_vec(hxi, hyi, hzi, P.xy(HB, o8), hzj, k, dx, dy, dz);
                     const float2 fs = pair_fs(pair_r2(dx, dy, dz, k), k, ri, ir2, ir6, ir8);
                     hvp_term(dx, dy, dz, fs, pair_nbc(ri, ir2, ir6, ir8, k), P.rxy(o8), P.rz(o8),
                              vix, viy, viz, hx, hy, hz);
@@ -500,11 +535,11 @@ struct PairList {
                 if (DO_F) {
                     float2 dx, dy, dz, ri, ir2, ir6, ir8;
                     if (SK && DO_H)
-                        pair_vec_given(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, sx, sy, sz, dx, dy, dz);
+                        pair_vec_given(fxi, fyi, fzi, P.xy(FB, o8), fzj, k, sx, sy, sz, dx, dy, dz);
                     else if (SK)
-                        pair_vec_shift(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz, sx, sy, sz);
+                        pair_vec_shift(fxi, fyi, fzi, P.xy(FB, o8), fzj, k, dx, dy, dz, sx, sy, sz);
                     else
-                        pair_vec(fxi, fyi, fzi, P.xy(fb, o8), P.z(fb, o8), k, dx, dy, dz);
+                        pair_vec(fxi, fyi, fzi, P.xy(FB, o8), fzj, k, dx, dy, dz);
                     const float2 r2 = pair_r2(dx, dy, dz, k);
                     if (HS) o |= (r2.x <= hs2.x) | (r2.y <= hs2.y);
                     const float2 fs = pair_fs(r2, k, ri, ir2, ir6, ir8);
@@ -850,11 +885,11 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
     {
         float2 hx, hy, hz, fx, fy, fz;
         if (sk)
-            L.template combined<false, true, true, HS>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx,
-                                                       hy, hz, fx, fy, fz, hs_pair(ts), &ov);
+            L.template combined<false, true, true, HS, 0, 0>(P, pk(0.0f), pk(0.0f), pk(0.0f), k, hx,
+                                                             hy, hz, fx, fy, fz, hs_pair(ts), &ov);
         else
-            L.template combined<false, true, false, HS>(P, 0, 0, pk(0.0f), pk(0.0f), pk(0.0f), k, hx,
-                                                        hy, hz, fx, fy, fz, hs_pair(ts), &ov);
+            L.template combined<false, true, false, HS, 0, 0>(P, pk(0.0f), pk(0.0f), pk(0.0f), k, hx,
+                                                              hy, hz, fx, fy, fz, hs_pair(ts), &ov);
         residual(0, ts, fx, fy, fz, rx, ry, rz);
         account(ts, rx, ry, rz);
     }
@@ -872,16 +907,27 @@ __device__ __forceinline__ void paired_item_pipe(const LJItem& I, const LJSysDev
         if (pf) fetch(a + 4, threadIdx.x, nv);
 
         float2 hx, hy, hz, fx, fy, fz;
-        if (next && sk)
-            L.template combined<true, true, true, HS>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy,
-                                                      fz, hs_pair(a + 2), &ov);
-        else if (next)
-            L.template combined<true, true, false, HS>(P, cur, nxt, rx, ry, rz, k, hx, hy, hz, fx, fy,
-                                                       fz, hs_pair(a + 2), &ov);
-        else if (sk)
-            L.template combined<true, false, true>(P, cur, cur, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+        // buffer indices as template arguments: immediate shared-memory offsets and
+        // a compile-time choice of the halves of the shared z slot
+        auto walk = [&](auto cur_c) {
+            constexpr int C = decltype(cur_c)::value;
+            if (next && sk)
+                L.template combined<true, true, true, HS, C, C ^ 1>(P, rx, ry, rz, k, hx, hy, hz, fx,
+                                                                    fy, fz, hs_pair(a + 2), &ov);
+            else if (next)
+                L.template combined<true, true, false, HS, C, C ^ 1>(P, rx, ry, rz, k, hx, hy, hz, fx,
+                                                                     fy, fz, hs_pair(a + 2), &ov);
+            else if (sk)
+                L.template combined<true, false, true, false, C, C>(P, rx, ry, rz, k, hx, hy, hz, fx,
+                                                                    fy, fz);
+            else
+                L.template combined<true, false, false, false, C, C>(P, rx, ry, rz, k, hx, hy, hz, fx,
+                                                                     fy, fz);
+        };
+        if (cur)
+            walk(std::integral_constant<int, 1>{});
         else
-            L.template combined<true, false, false>(P, cur, cur, rx, ry, rz, k, hx, hy, hz, fx, fy, fz);
+            walk(std::integral_constant<int, 0>{});
         if (lead) {
             const float2 gx = mul2(fma2(pk(k.a), hx, sub2(pk(rpx, rx.x), rx)), ginv);
             const float2 gy = mul2(fma2(pk(k.a), hy, sub2(pk(rpy, ry.x), ry)), ginv);

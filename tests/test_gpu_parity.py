@@ -4,6 +4,7 @@ Tolerances: FP32 data with FP64 accumulation, 1e-5 relative on S and on the
 gradient (per chain, 2-norm) plus a max-abs bound of 1e-5 * max|g|; plain FP64,
 1e-12 relative.  Index work (pair counts, Philox words) is compared bit for bit.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -143,6 +144,30 @@ def test_results_independent_of_tiling(pamd, name):
     for S, g in outs[1:]:
         assert torch.equal(S, outs[0][0])
         assert torch.equal(g, outs[0][1])
+
+
+@pytest.mark.parametrize("tpp", [0, 1, 2, 4])
+def test_threads_per_particle_match_the_oracle(pamd, tpp):
+    """Every width of the per-particle thread group against the oracle: forced
+    widths 1, 2 and 4, and the automatic choice (0), which gives the two tiny
+    systems added to the small ragged batch (N = 16, 20) groups of 8 threads.
+    Candidate classes are split over the group below 8 threads and lie in one
+    class per thread at 8.  A list capacity of 24 sends most particles down the
+    overflow paths."""
+    base = inputs.workload("ragged", "small")
+    tiny = [inputs.SystemSpec("lj", n, 3, 40, 1) for n in (16, 20)]
+    w = dataclasses.replace(base, systems=list(base.systems) + tiny)
+    paths = start_paths(w, "fp32")
+    try:
+        for maxnb in (0, 24):
+            pamd.tune(0, tpp, maxnb, -1.0, 0)
+            prob = _problem(pamd, w, "fp32")
+            buf = _upload(pamd, prob, paths)
+            S, g = pamd.action_grad(prob, buf)
+            torch.cuda.synchronize()
+            _check_against_oracle(w, prob, paths, S, g, 1e-5)
+    finally:
+        pamd.tune()
 
 
 def test_lj_far_from_brownian_paths_use_the_fallbacks(pamd):
