@@ -557,9 +557,12 @@ def main():
         del scratch, hscratch
         e2e_clocks = ClockSampler(local)
         e2e_clocks.start()
+        step_ms = []
         t0 = time.perf_counter()
         for i in range(ne):
+            t1 = time.perf_counter()
             pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=6 + i, n_accepted=hacc)
+            step_ms.append((time.perf_counter() - t1) * 1e3)
         t_e2e = (time.perf_counter() - t0) / ne
         e2e_clk = e2e_clocks.stop()
         nbuf = prob.span * 4
@@ -568,7 +571,10 @@ def main():
         e2e = {"value": units_rank * world / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
                "d2h_bytes_per_step": 2 * nbuf + 8 * prob.n_chains + 4 * prob.n_chains,
-               "ms_per_step": t_e2e * 1e3, "sm_mhz": e2e_clk.get("sm_mhz"),
+               "ms_per_step": t_e2e * 1e3,
+               "step_ms": [round(v, 2) for v in step_ms],
+               "median_ms_per_step": round(statistics.median(step_ms), 3),
+               "sm_mhz": e2e_clk.get("sm_mhz"),
                "pinned_copy_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)},
                "pipeline": {"lanes": int(os.environ.get("PAMD_PIPE_LANES", "3")),
                             "last_step_device_ms": round(total_ms, 3),
