@@ -71,6 +71,22 @@ struct SysInfo {
     long long first_slice = 0;   // time slab (0 / 0 / 0 for whole paths)
     int halo_lo = 0, halo_hi = 0;
     long long hs_off = 0;        // LJ: first of its slices in the hard-sphere radii array
+    int lj_class = 0;            // LJ: block-size class (launch) of the system
+    int NT = 0;                  // LJ: block size of that class
+};
+
+// LJ systems launched together: one block size, shared-memory size and grid.
+// Single-precision batches that mix systems of N <= 512 and N > 512 get two
+// classes, so the smaller systems run the pipelined 512-thread kernel instead of
+// leaving most of a 1024-thread block idle.
+struct LJClass {
+    int NT = 0, nmax = 0, grid_grad = 0, grid_nograd = 0;
+    bool pipe = false;           // gradient pass pipelined over step pairs
+    size_t smem = 0;
+    long long outer_words = 0;   // 32-bit words of each CTA's outer-list region
+    int item_off = 0, n_items = 0;  // its items in d_lj_items (cost-sorted)
+    int grp_off = 0;             // its items in d_lj_items_grp (grouped by chain)
+    std::vector<int> grp_first;  // per global chain c: [grp_first[c], grp_first[c + 1]), relative
 };
 
 // Buffers and update count of a captured update graph.  Compared field by field:
@@ -107,20 +123,17 @@ struct Plan {
     double* d_part_S = nullptr;
     double* d_part_qf = nullptr;
     double* d_part_qr = nullptr;
-    // LJ work items (persistent kernel)
-    int lj_NT = 0, lj_nmax = 0, lj_grid_grad = 0, lj_grid_nograd = 0;
+    // LJ work items (persistent kernels, one launch per block-size class)
     bool lj_paired = false;  // single precision: two steps per thread (lj_paired.cu)
-    bool lj_pipe = false;    // ... with the gradient pass pipelined over step pairs
-    size_t lj_smem = 0;
+    std::vector<LJClass> lj_cls;
     std::vector<unsigned char> h_lj_sys;  // host copy of the system table
     size_t lj_sys_stride = 0;
     void* d_lj_sys = nullptr;
     LJItem* d_lj_items = nullptr;
     int n_lj_items = 0;
     std::vector<int> lj_chain_first, lj_chain_count;  // per global chain (plain form)
-    // the same items grouped by chain: chain c owns [lj_grp_first[c], lj_grp_first[c + 1])
-    std::vector<int> lj_grp_first;
-    LJItem* d_lj_items_grp = nullptr;
+    std::vector<int> lj_chain_class;                  // per global chain: its class (-1: none)
+    LJItem* d_lj_items_grp = nullptr;  // the same items, per class grouped by chain
     std::vector<ChainSlots> h_E_slots;  // per chain: its element blocks in h_all
     int* d_counter = nullptr;
     int* d_err = nullptr;  // device status word (PAMD_OK or PAMD_ERR_NONFINITE)
@@ -143,8 +156,9 @@ struct Plan {
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::vector<void*> allocs;
     // paired LJ kernel: outer lists, one set per compute lane of one region per CTA
+    // (the classes of a lane run one after another and share its set)
     uint32_t* d_outer = nullptr;
-    long long outer_words = 0;  // 32-bit words per CTA region
+    long long outer_lane_words = 0;  // 32-bit words of one lane's set
     int n_lanes = 1;            // compute lanes of the host-buffer pipeline
     // hard-sphere path bias (pamd_action_grad_hs): radii of every LJ slice, per-chain flags
     long long hs_slices = 0;
@@ -286,13 +300,10 @@ int max_dynamic_smem()
     return v;
 }
 
-// Block size shared by every LJ system of a problem: the largest N rounded up
-// to a warp multiple (at least 128); blocks of <= 512 threads run two per SM.
-int choose_lj_block(const pamd_problem* p)
+// Block size of a class of LJ systems: its largest N rounded up to a warp
+// multiple (at least 128).
+int choose_lj_block(int nmax)
 {
-    int nmax = 0;
-    for (int q = 0; q < p->n_systems; ++q)
-        if (p->systems[q].pot.kind == PAMD_LJ) nmax = std::max(nmax, p->systems[q].n_particles);
     int NT = std::max(128, ((nmax + 31) / 32) * 32);
     if (g_tune_override.tpp > 0) NT = std::max(NT, std::min(1024, ((nmax * g_tune_override.tpp + 31) / 32) * 32));
     return NT;
@@ -478,66 +489,80 @@ int build_plan(const pamd_problem* p, Plan** out)
         }
     }
     int slot = (int)P->h_ho.size();
-    // LJ: common block size, shared-memory budget, per-system shapes, items.
+    // LJ: block-size classes, shared-memory budgets, per-system shapes, items.
     std::vector<LJItem> items, grouped;
-    std::vector<int> item_chain;  // global chain of each item
     P->lj_chain_first.assign(chain, -1);
     P->lj_chain_count.assign(chain, 0);
+    P->lj_chain_class.assign(chain, -1);
+    P->lj_cls.clear();
     {
         const bool one = (p->flags & PAMD_FLAG_ONE_CHAIN_PER_LAUNCH) != 0;
-        int nlj = 0, nmax = 0;
+        int nlj = 0, n_small = 0, n_big = 0;
         for (auto& si : P->sys)
             if (si.kind == PAMD_LJ) {
                 si.lj_index = nlj++;
-                nmax = std::max(nmax, si.N);
+                (si.N <= 512 ? n_small : n_big) += 1;
             }
         if (nlj) {
-            const int NT = choose_lj_block(p);
-            const size_t v4 = P->fp64 ? 32 : 16;
-            // Single precision runs the paired-step kernel, one CTA per SM: its lists
-            // may use all the shared memory beside the packed slices (48 bytes per
-            // particle slot, 88 in the pipelined gradient form).
             P->lj_paired = !P->fp64 && std::getenv("PAMD_LJ_ONE_STEP") == nullptr;
-            P->lj_pipe = P->lj_paired && NT <= 512 && std::getenv("PAMD_LJ_NO_PIPE") == nullptr;
-            const long long slices = P->lj_paired ? (P->lj_pipe ? 88LL * 512 : 48LL * (NT <= 512 ? 512 : 1024))
-                                                  : 3 * (long long)nmax * v4;
-            const int budget = (NT <= 512 && !P->fp64 && !P->lj_paired && g_tune_override.maxnb <= 0)
-                                   ? 113 * 1024
-                                   : max_dynamic_smem() - 1024;
-            // (the one-step Euler kernel shares the capacity: its slices must fit too)
-            const long long slices_euler = 3 * (long long)nmax * v4;
-            const int cap_lane_max = std::max(
-                1, (int)((budget - std::max(slices, slices_euler)) / (2 * (long long)NT)));
-            int cap_used = 1;
-            std::vector<double> cost;
-            for (int q = 0; q < (int)P->sys.size(); ++q) {
-                SysInfo& si = P->sys[q];
-                if (si.kind != PAMD_LJ) continue;
-                si.tune = choose_lj_tune(p->systems[q], NT, cap_lane_max, P->lj_paired,
-                                         std::sqrt(2.0 * p->D * p->dt));
-                cap_used = std::max(cap_used, si.tune.maxnb);
-            }
-            P->lj_NT = NT;
-            P->lj_nmax = nmax;
-            P->lj_smem = P->lj_paired ? lj_paired_smem_bytes(NT, cap_used, P->lj_pipe)
-                                      : lj_smem_bytes(nmax, NT, cap_used, P->fp64);
+            const bool split = P->lj_paired && n_small && n_big && std::getenv("PAMD_LJ_ONE_CLASS") == nullptr;
+            P->lj_cls.resize(split ? 2 : 1);
+            for (auto& si : P->sys)
+                if (si.kind == PAMD_LJ) si.lj_class = (split && si.N > 512) ? 1 : 0;
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int bg = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, true, P->lj_pipe)
-                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, true)
-                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, true);
-            const int bn = P->lj_paired ? lj_paired_blocks_per_sm(NT, P->lj_smem, false, P->lj_pipe)
-                           : P->fp64    ? lj_blocks_per_sm<double>(NT, P->lj_smem, false)
-                                        : lj_blocks_per_sm<float>(NT, P->lj_smem, false);
-            if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
+            const size_t v4 = P->fp64 ? 32 : 16;
+            std::vector<int> bg_cls(P->lj_cls.size(), 0);
+            for (int k = 0; k < (int)P->lj_cls.size(); ++k) {
+                LJClass& C = P->lj_cls[k];
+                for (auto& si : P->sys)
+                    if (si.kind == PAMD_LJ && si.lj_class == k) C.nmax = std::max(C.nmax, si.N);
+                const int NT = choose_lj_block(C.nmax);
+                const int nmax = C.nmax;
+                // Single precision runs the paired-step kernel, one CTA per SM: its lists
+                // may use all the shared memory beside the packed slices (48 bytes per
+                // particle slot, 88 in the pipelined gradient form).
+                C.NT = NT;
+                C.pipe = P->lj_paired && NT <= 512 && std::getenv("PAMD_LJ_NO_PIPE") == nullptr;
+                const long long slices = P->lj_paired ? (C.pipe ? 88LL * 512 : 48LL * (NT <= 512 ? 512 : 1024))
+                                                      : 3 * (long long)nmax * v4;
+                const int budget = (NT <= 512 && !P->fp64 && !P->lj_paired && g_tune_override.maxnb <= 0)
+                                       ? 113 * 1024
+                                       : max_dynamic_smem() - 1024;
+                // (the one-step Euler kernel shares the capacity: its slices must fit too)
+                const long long slices_euler = 3 * (long long)nmax * v4;
+                const int cap_lane_max = std::max(
+                    1, (int)((budget - std::max(slices, slices_euler)) / (2 * (long long)NT)));
+                int cap_used = 1;
+                for (int q = 0; q < (int)P->sys.size(); ++q) {
+                    SysInfo& si = P->sys[q];
+                    if (si.kind != PAMD_LJ || si.lj_class != k) continue;
+                    si.tune = choose_lj_tune(p->systems[q], NT, cap_lane_max, P->lj_paired,
+                                             std::sqrt(2.0 * p->D * p->dt));
+                    si.NT = NT;
+                    cap_used = std::max(cap_used, si.tune.maxnb);
+                }
+                C.smem = P->lj_paired ? lj_paired_smem_bytes(NT, cap_used, C.pipe)
+                                      : lj_smem_bytes(nmax, NT, cap_used, P->fp64);
+                const int bg = P->lj_paired ? lj_paired_blocks_per_sm(NT, C.smem, true, C.pipe)
+                               : P->fp64    ? lj_blocks_per_sm<double>(NT, C.smem, true)
+                                            : lj_blocks_per_sm<float>(NT, C.smem, true);
+                const int bn = P->lj_paired ? lj_paired_blocks_per_sm(NT, C.smem, false, C.pipe)
+                               : P->fp64    ? lj_blocks_per_sm<double>(NT, C.smem, false)
+                                            : lj_blocks_per_sm<float>(NT, C.smem, false);
+                if (bg <= 0 || bn <= 0) return PAMD_ERR_UNSUPPORTED;
+                bg_cls[k] = bg;
+                C.grid_grad = bg * sms;  // trimmed to the item count below
+                C.grid_nograd = bn * sms;
+            }
             // One LJ system of equal items: pick the tile near the chosen one whose item
             // count fills whole rounds of the persistent grid (no part-empty last round),
             // keeping at least 16 steps per item.
             if (nlj == 1 && !one) {
                 for (auto& si : P->sys) {
                     if (si.kind != PAMD_LJ) continue;
-                    const long long G = (long long)bg * sms;
+                    const long long G = (long long)bg_cls[si.lj_class] * sms;
                     const int Tow = si.T - si.halo_lo;  // owned steps
                     const long long items0 = (long long)si.chains * ((Tow + si.tune.tile_steps - 1) / si.tune.tile_steps);
                     const long long rounds = (items0 + G - 1) / G;
@@ -548,6 +573,9 @@ int build_plan(const pamd_problem* p, Plan** out)
                     }
                 }
             }
+            // Items of every system (S slots in system order), with their cost.
+            std::vector<std::vector<LJItem>> sys_items(P->sys.size());
+            std::vector<std::vector<double>> sys_cost(P->sys.size());
             for (int q = 0; q < (int)P->sys.size(); ++q) {
                 SysInfo& si = P->sys[q];
                 if (si.kind != PAMD_LJ) continue;
@@ -557,8 +585,8 @@ int build_plan(const pamd_problem* p, Plan** out)
                     const int c = si.chain0 + b;
                     Sslots[c].begin = slot + b * si.n_tiles;
                     Sslots[c].end = slot + (b + 1) * si.n_tiles;
-                    P->lj_chain_first[c] = (int)items.size();
                     P->lj_chain_count[c] = si.n_tiles;
+                    P->lj_chain_class[c] = si.lj_class;
                     for (int tl = 0; tl < si.n_tiles; ++tl) {
                         LJItem it;
                         it.sys = si.lj_index;
@@ -566,43 +594,68 @@ int build_plan(const pamd_problem* p, Plan** out)
                         it.t0 = si.halo_lo + tl * si.tune.tile_steps;  // owned steps only
                         it.t1 = std::min(si.T, it.t0 + si.tune.tile_steps);
                         it.slot = slot + b * si.n_tiles + tl;
-                        items.push_back(it);
-                        item_chain.push_back(c);
-                        cost.push_back((double)si.N * si.tune.maxnb * si.tune.tpp * (it.t1 - it.t0 + 1));
+                        sys_items[q].push_back(it);
+                        sys_cost[q].push_back((double)si.N * si.tune.maxnb * si.tune.tpp * (it.t1 - it.t0 + 1));
                     }
                 }
                 slot += si.chains * si.n_tiles;
             }
-            // Chain-grouped copy (chains in order, each chain's items largest first) for
-            // launches over a range of chains.
-            {
-                std::vector<int> ord(items.size());
+            // Per class: its items (largest first unless one chain per launch) and a
+            // copy grouped by chain (chains in order, each chain's items largest first)
+            // for launches over a range of chains.
+            for (int k = 0; k < (int)P->lj_cls.size(); ++k) {
+                LJClass& C = P->lj_cls[k];
+                std::vector<LJItem> ci;
+                std::vector<double> cc;
+                std::vector<int> cchain;
+                for (int q = 0; q < (int)P->sys.size(); ++q) {
+                    const SysInfo& si = P->sys[q];
+                    if (si.kind != PAMD_LJ || si.lj_class != k) continue;
+                    for (size_t m = 0; m < sys_items[q].size(); ++m) {
+                        const int c = si.chain0 + sys_items[q][m].chain;
+                        if (P->lj_chain_first[c] < 0) P->lj_chain_first[c] = (int)(items.size() + ci.size());
+                        ci.push_back(sys_items[q][m]);
+                        cc.push_back(sys_cost[q][m]);
+                        cchain.push_back(c);
+                    }
+                }
+                std::vector<int> ord(ci.size());
                 for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
-                std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-                    const int ca = item_chain[a], cb = item_chain[b];
-                    return ca != cb ? ca < cb : cost[a] > cost[b];
+                std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+                    return cchain[x] != cchain[y] ? cchain[x] < cchain[y] : cc[x] > cc[y];
                 });
-                for (int q : ord) grouped.push_back(items[q]);
+                C.grp_off = (int)grouped.size();
+                C.grp_first.assign(chain + 1, 0);
+                for (int q : ord) {
+                    grouped.push_back(ci[q]);
+                    ++C.grp_first[cchain[q] + 1];
+                }
+                for (int c = 0; c < chain; ++c) C.grp_first[c + 1] += C.grp_first[c];
+                if (!one) {  // largest items first
+                    for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+                    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cc[x] > cc[y]; });
+                    std::vector<LJItem> sorted;
+                    for (int q : ord) sorted.push_back(ci[q]);
+                    ci.swap(sorted);
+                }
+                C.item_off = (int)items.size();
+                C.n_items = (int)ci.size();
+                items.insert(items.end(), ci.begin(), ci.end());
+                C.grid_grad = std::max(1, std::min(C.n_items, C.grid_grad));
+                C.grid_nograd = std::max(1, std::min(C.n_items, C.grid_nograd));
             }
-            if (!one) {  // largest items first
-                std::vector<int> ord(items.size());
-                for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
-                std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-                std::vector<LJItem> sorted;
-                for (int q : ord) sorted.push_back(items[q]);
-                items.swap(sorted);
-            }
-            P->lj_grid_grad = std::max(1, std::min((int)items.size(), bg * sms));
-            P->lj_grid_nograd = std::max(1, std::min((int)items.size(), bn * sms));
             if (P->lj_paired) {
-                int ocap = 2;
-                for (auto& si : P->sys)
-                    if (si.kind == PAMD_LJ) ocap = std::max(ocap, si.tune.outer_cap);
-                P->outer_words = (long long)(ocap / 2) * NT;
                 P->n_lanes = pipeline_lanes();
-                const long long grid = std::max(P->lj_grid_grad, P->lj_grid_nograd);
-                if ((rc0 = P->alloc(&P->d_outer,
-                                    sizeof(uint32_t) * P->n_lanes * grid * P->outer_words)))
+                for (auto& C : P->lj_cls) {
+                    int ocap = 2;
+                    for (auto& si : P->sys)
+                        if (si.kind == PAMD_LJ && &P->lj_cls[si.lj_class] == &C)
+                            ocap = std::max(ocap, si.tune.outer_cap);
+                    C.outer_words = (long long)(ocap / 2) * C.NT;
+                    P->outer_lane_words = std::max(P->outer_lane_words,
+                                                   (long long)std::max(C.grid_grad, C.grid_nograd) * C.outer_words);
+                }
+                if ((rc0 = P->alloc(&P->d_outer, sizeof(uint32_t) * P->n_lanes * P->outer_lane_words)))
                     return rc0;
             }
             if (P->fp64)
@@ -610,21 +663,20 @@ int build_plan(const pamd_problem* p, Plan** out)
             else
                 fill_lj_sys<float>(P.get(), p);
             if (std::getenv("PAMD_DEBUG_PLAN")) {
-                std::fprintf(stderr, "pamd plan: paired=%d NT=%d nmax=%d smem=%zu blocks/SM grad=%d nograd=%d "
-                             "grid=%d items=%zu\n", (int)P->lj_paired, NT, nmax, P->lj_smem, bg, bn, P->lj_grid_grad,
-                             items.size());
+                for (auto& C : P->lj_cls)
+                    std::fprintf(stderr, "pamd plan: paired=%d class NT=%d nmax=%d pipe=%d smem=%zu grid grad=%d "
+                                 "nograd=%d items=%d\n", (int)P->lj_paired, C.NT, C.nmax, (int)C.pipe, C.smem,
+                                 C.grid_grad, C.grid_nograd, C.n_items);
                 for (auto& si : P->sys)
                     if (si.kind == PAMD_LJ)
-                        std::fprintf(stderr, "  N=%d T=%d tpp=%d cap/thread=%d skin=%.3f tile=%d\n",
-                                     si.N, si.T, si.tune.tpp, si.tune.maxnb, si.tune.skin,
+                        std::fprintf(stderr, "  N=%d T=%d class=%d tpp=%d cap/thread=%d skin=%.3f tile=%d\n",
+                                     si.N, si.T, si.lj_class, si.tune.tpp, si.tune.maxnb, si.tune.skin,
                                      si.tune.tile_steps);
             }
         }
     }
     P->n_lj_items = (int)items.size();
     P->n_S_slots = slot;
-    P->lj_grp_first.assign(chain + 1, 0);
-    for (int c = 0; c < chain; ++c) P->lj_grp_first[c + 1] = P->lj_grp_first[c] + P->lj_chain_count[c];
     P->h_E_slots = Eslots;
     int rc;
     if ((rc = P->alloc(&P->d_all, sizeof(ElemBlock) * P->h_all.size()))) return rc;
@@ -732,31 +784,32 @@ int run_action(const pamd_problem* p, Plan* P, const R* pos, R* grad, double* S_
             if ((rc = ho(b0, b1 - b0))) return rc;
         }
     }
-    if (P->n_lj_items > 0) {
-        const int grid = with_grad ? P->lj_grid_grad : P->lj_grid_nograd;
+    // LJ systems: one persistent launch per block-size class, one after another on st
+    for (int k = 0; k < (int)P->lj_cls.size(); ++k) {
+        const LJClass& C = P->lj_cls[k];
+        if (C.n_items <= 0) continue;
+        const int grid = with_grad ? C.grid_grad : C.grid_nograd;
         auto launch = [&](const LJItem* items, int n, int g) {
             if (std::is_same<R, float>::value && P->lj_paired)
-                return launch_lj_paired(
-                    items, n, P->d_lj_sys, (const float*)pos, (float*)grad, P->d_part_S, counter,
-                    P->lj_NT, P->lj_smem, g, with_grad, P->lj_pipe,
-                    P->d_outer + (long long)lane * std::max(P->lj_grid_grad, P->lj_grid_nograd) *
-                                     P->outer_words,
-                    P->outer_words, st, (const float*)hs2, overlap);
-            return launch_lj_items<R>(items, n, P->d_lj_sys, P->lj_nmax, pos, grad, P->d_part_S,
-                                      counter, P->lj_NT, P->lj_smem, g, with_grad, st, hs2, overlap);
+                return launch_lj_paired(items, n, P->d_lj_sys, (const float*)pos, (float*)grad,
+                                        P->d_part_S, counter, C.NT, C.smem, g, with_grad, C.pipe,
+                                        P->d_outer + (long long)lane * P->outer_lane_words,
+                                        C.outer_words, st, (const float*)hs2, overlap);
+            return launch_lj_items<R>(items, n, P->d_lj_sys, C.nmax, pos, grad, P->d_part_S, counter,
+                                      C.NT, C.smem, g, with_grad, st, hs2, overlap);
         };
         if (one) {
             for (int c = c0; c < c1; ++c) {
                 const int f = P->lj_chain_first[c];
-                if (f < 0) continue;
+                if (f < 0 || P->lj_chain_class[c] != k) continue;
                 const int n = P->lj_chain_count[c];
                 PAMD_CUDA_TRY(launch(P->d_lj_items + f, n, std::min(grid, n)));
             }
         } else if (all) {
-            PAMD_CUDA_TRY(launch(P->d_lj_items, P->n_lj_items, grid));
+            PAMD_CUDA_TRY(launch(P->d_lj_items + C.item_off, C.n_items, grid));
         } else {
-            const int f = P->lj_grp_first[c0], n = P->lj_grp_first[c1] - f;
-            if (n > 0) PAMD_CUDA_TRY(launch(P->d_lj_items_grp + f, n, std::min(grid, n)));
+            const int f = C.grp_first[c0], n = C.grp_first[c1] - f;
+            if (n > 0) PAMD_CUDA_TRY(launch(P->d_lj_items_grp + C.grp_off + f, n, std::min(grid, n)));
         }
     }
     PAMD_CUDA_TRY(launch_finalize(P->d_part_S, P->d_S_slots + c0, c1 - c0, 1.0 / (4.0 * p->D * p->dt),
@@ -1395,14 +1448,14 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
                                                      sig, seed, counter, st));
         } else {
             const void* row = &P->h_lj_sys[P->lj_sys_stride * si.lj_index];
-            const size_t smem = lj_smem_bytes(si.N, P->lj_NT, si.tune.maxnb, P->fp64);
+            const size_t smem = lj_smem_bytes(si.N, si.NT, si.tune.maxnb, P->fp64);
             if (P->fp64)
                 PAMD_CUDA_TRY(launch_lj_euler<double>((double*)dpos, (const double*)dnoise, row,
-                                                      P->lj_NT, smem, si.chains, si.chain0, seed,
+                                                      si.NT, smem, si.chains, si.chain0, seed,
                                                       counter, st));
             else
                 PAMD_CUDA_TRY(launch_lj_euler<float>((float*)dpos, (const float*)dnoise, row,
-                                                     P->lj_NT, smem, si.chains, si.chain0, seed,
+                                                     si.NT, smem, si.chains, si.chain0, seed,
                                                      counter, st));
         }
     }

@@ -41,6 +41,17 @@ def _upload(pamd, prob, paths, device="cuda"):
     return buf
 
 
+def _workload(name):
+    """The small workloads, plus "mixed": LJ systems on both sides of N = 512, which
+    a single-precision plan launches in two block-size classes."""
+    if name == "mixed":
+        base = inputs.workload("ragged", "small")
+        systems = [inputs.SystemSpec("lj", 96, 3, 40, 2), inputs.SystemSpec("lj", 530, 3, 33, 1),
+                   inputs.SystemSpec("lj", 700, 3, 25, 2)]
+        return dataclasses.replace(base, name="mixed", systems=systems)
+    return inputs.workload(name, "small")
+
+
 def _check_against_oracle(w, prob, paths, S, g, tol_rel, nthreads=8):
     S = S.cpu().numpy()
     g = g.cpu()
@@ -168,6 +179,34 @@ def test_threads_per_particle_match_the_oracle(pamd, tpp):
             _check_against_oracle(w, prob, paths, S, g, 1e-5)
     finally:
         pamd.tune()
+
+
+@pytest.mark.parametrize("one_class", [False, True])
+def test_block_size_classes_match_the_oracle(pamd, parity_report, one_class):
+    """A single-precision batch of LJ systems with N on both sides of 512 runs in two
+    persistent launches (the N <= 512 systems in 128-thread blocks with the pipelined
+    gradient pass, the others in 704-thread blocks); PAMD_LJ_ONE_CLASS keeps one
+    launch of 704-thread blocks.  Both against the oracle, and in one chain per
+    launch."""
+    import os
+    w = _workload("mixed")
+    paths = start_paths(w, "fp32")
+    try:
+        if one_class:
+            os.environ["PAMD_LJ_ONE_CLASS"] = "1"
+        for one in (False, True):
+            pamd.release_cache()
+            prob = _problem(pamd, w, "fp32", one=one)
+            buf = _upload(pamd, prob, paths)
+            S, g = pamd.action_grad(prob, buf)
+            torch.cuda.synchronize()
+            es, eg, em = _check_against_oracle(w, prob, paths, S, g, 1e-5)
+            if not one and not one_class:
+                parity_report.record("mixed_classes", "test_block_size_classes_match_the_oracle",
+                                     S_rel=es, grad_rel_2norm=eg, grad_rel_maxabs=em)
+    finally:
+        os.environ.pop("PAMD_LJ_ONE_CLASS", None)
+        pamd.release_cache()
 
 
 def test_lj_far_from_brownian_paths_use_the_fallbacks(pamd):
@@ -377,13 +416,14 @@ def test_host_buffers_match_device_buffers(pamd):
 
 @pytest.mark.parametrize("name,precision,n_updates",
                          [("ragged", "fp32", 1), ("ragged", "fp64", 2), ("lj500", "fp32", 3),
-                          ("ho3d", "fp32", 2)])
+                          ("ho3d", "fp32", 2), ("mixed", "fp32", 2)])
 def test_path_update_host_buffers_match_device_buffers(pamd, name, precision, n_updates):
     """With host buffers the update is pipelined over chunks of chains (copies of one
     chunk overlap the updates of another); every chain must come out bit for bit as
     from one update over device buffers.  The host-side S, acceptance counts and
-    log alpha are covered, and a mix of host and device buffers."""
-    w = inputs.workload(name, "small")
+    log alpha are covered, and a mix of host and device buffers.  "mixed" runs two
+    block-size classes per chunk."""
+    w = _workload(name)
     paths = start_paths(w, precision)
     prob = _problem(pamd, w, precision)
     h = 2e-7 if name != "ho3d" else 1e-5
