@@ -382,10 +382,24 @@ int pamd_device_status(void* stream);
  * keeps the automatic choice): steps per CTA tile, threads per particle
  * (1, 2 or 4), neighbour-list capacity per particle, Verlet skin (sigma
  * units; double precision), steps per neighbour-list window (single
- * precision; >= 2).  Affects plans built afterwards; results do not depend
- * on these (candidate order is fixed), only speed.  PAMD_ERR_ARG for a
- * negative size, an unsupported thread count or a window of 1.  Host-side
- * setting, not thread-safe against concurrent calls. */
+ * precision; >= 2).  Affects plans built afterwards.  Results do not depend
+ * on the tile, capacity, skin or window (candidate order is fixed); the
+ * number of threads per particle changes how a particle's force and
+ * Hessian sums are split, so results differ by rounding only.  PAMD_ERR_ARG
+ * for a negative size, an unsupported thread count or a window of 1.
+ * Host-side setting, not thread-safe against concurrent calls.
+ *
+ * Environment switches read when a plan is built (part of the plan's key, so
+ * a change takes effect at the next call):
+ *   PAMD_LJ_NO_PIPE=1        single precision: the two-pass gradient form
+ *                            instead of the pipelined one (bitwise equal);
+ *   PAMD_LJ_PER_STEP_SHIFT=1 single precision: the minimum image rounded at
+ *                            every slice (bitwise equal);
+ *   PAMD_LJ_ONE_CLASS=1      single precision: one launch for all LJ systems
+ *                            instead of one per block-size class;
+ *   PAMD_LJ_ONE_STEP=1       single precision through the one-step kernel;
+ *   PAMD_PIPE_LANES=n        compute lanes of the host-buffer update pipeline
+ *                            (1..4, default 3). */
 int pamd_tune(int tile_steps, int threads_per_particle, int max_neighbours, double skin,
               int window_steps);
 

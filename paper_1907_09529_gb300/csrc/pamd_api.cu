@@ -280,7 +280,13 @@ std::string plan_key(const pamd_problem* p)
     os << p->precision << '|' << p->flags << '|' << p->D << ',' << p->beta << ',' << p->dt << '|'
        << p->n_systems << '|' << g_tune_override.tile_steps
        << ',' << g_tune_override.tpp << ',' << g_tune_override.maxnb << ',' << g_tune_override.skin
-       << ',' << g_tune_override.window;
+       << ',' << g_tune_override.window << '|';
+    // launch-shape switches read when a plan is built: a change builds a new plan
+    for (const char* v : {"PAMD_LJ_ONE_STEP", "PAMD_LJ_NO_PIPE", "PAMD_LJ_ONE_CLASS",
+                          "PAMD_LJ_PER_STEP_SHIFT", "PAMD_PIPE_LANES"}) {
+        const char* e = std::getenv(v);
+        os << (e ? e : "-") << ',';
+    }
     for (int q = 0; q < p->n_systems; ++q) {
         const pamd_system& s = p->systems[q];
         os << '|' << s.n_particles << ',' << s.n_steps << ',' << s.dim << ',' << s.n_chains << ','
