@@ -118,19 +118,23 @@ class TorchComm:
 
     def exchange(self, to_left: Sequence, to_right: Sequence):
         """to_left[0] goes to rank - 1, to_right[0] to rank + 1; returns what the
-        left and right neighbours sent this way ([None] at the ends)."""
+        left and right neighbours sent this way ([None] at the ends).  The sends
+        and receives are posted as one batch: NCCL runs the point-to-point
+        operations between two ranks in the order they are posted, so posting
+        them one by one (receive, then send, on both sides) would wait forever."""
         d, r = self.dist, self.rank
-        works, from_left, from_right = [], None, None
+        ops, from_left, from_right = [], None, None
         if r > 0:
             from_left = torch.empty_like(to_left[0])
-            works.append(d.irecv(from_left, src=r - 1))
-            works.append(d.isend(to_left[0].contiguous(), dst=r - 1))
+            ops.append(d.P2POp(d.irecv, from_left, r - 1))
+            ops.append(d.P2POp(d.isend, to_left[0].contiguous(), r - 1))
         if r < self.world - 1:
             from_right = torch.empty_like(to_right[0])
-            works.append(d.irecv(from_right, src=r + 1))
-            works.append(d.isend(to_right[0].contiguous(), dst=r + 1))
-        for w in works:
-            w.wait()
+            ops.append(d.P2POp(d.irecv, from_right, r + 1))
+            ops.append(d.P2POp(d.isend, to_right[0].contiguous(), r + 1))
+        if ops:
+            for w in d.batch_isend_irecv(ops):
+                w.wait()
         return [from_left], [from_right]
 
     def allreduce_sum(self, ts: Sequence[torch.Tensor]):
