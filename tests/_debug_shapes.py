@@ -5,8 +5,9 @@ bounds-check record.  test_gpu_debug_build runs it with the bounds-checked build
 Covered: action + gradient of every workload at its small size (single and
 double precision), the LJ kernel under several tiles, windows and list
 capacities (including the overflow paths, a path far from Brownian and the
-per-step image shift), path updates (captured graph and host-buffer pipeline),
-the multilevel sampler and the PAMD event, and time slabs.
+per-step image shift), a batch split into two block-size classes, path updates
+(captured graph and host-buffer pipeline), the multilevel sampler and the PAMD
+event, and time slabs.
 """
 import json
 import os
@@ -68,6 +69,27 @@ def main():
         run("lj108", "fp32", tune)
     run("lj500", "fp32", env={"PAMD_LJ_NO_PIPE": "1"})
     run("ragged", "fp32", env={"PAMD_LJ_PER_STEP_SHIFT": "1"})
+    # systems on both sides of N = 512: two block-size classes, each with its own
+    # block size and shared memory, sharing the outer-list region
+    import dataclasses
+    mixed = dataclasses.replace(
+        inputs.workload("ragged", "small"), name="mixed",
+        systems=[inputs.SystemSpec("lj", 96, 3, 40, 2), inputs.SystemSpec("lj", 530, 3, 33, 1),
+                 inputs.SystemSpec("lj", 700, 3, 25, 2)])
+    for prec in ("fp32", "fp64"):
+        pamd.release_cache()
+        prob = pamd.Problem([gpu_system(s, pamd) for s in mixed.systems], mixed.D, mixed.beta,
+                            mixed.dt, precision=prec)
+        paths = start_paths(mixed, prec)
+        buf = prob.empty("cuda")
+        for q, p in enumerate(paths):
+            prob.view(buf, q).copy_(torch.from_numpy(p).to(prob.dtype))
+        S, g = pamd.action_grad(prob, buf)
+        torch.cuda.synchronize()
+        check(mixed, prob, paths, S, g, prec)
+        if prec == "fp32":  # host-buffer pipeline over the two classes
+            hb, hg, hS = buf.cpu().pin_memory(), g.cpu().pin_memory(), S.cpu().pin_memory()
+            pamd.path_update(prob, hb, hg, hS, 2e-7, n_updates=1, seed=1, counter=3)
 
     # a path far from Brownian: outer and window lists overflow
     N, T, B = 256, 40, 2

@@ -33,7 +33,13 @@ def pamd():
 
 
 def _setup(pamd, name, precision):
-    w = inputs.workload(name, "small")
+    if name == "mixed":  # LJ systems on both sides of N = 512: two block-size classes
+        import dataclasses
+        w = dataclasses.replace(
+            inputs.workload("ragged", "small"), name="mixed",
+            systems=[inputs.SystemSpec("lj", 96, 3, 30, 2), inputs.SystemSpec("lj", 600, 3, 20, 2)])
+    else:
+        w = inputs.workload(name, "small")
     prob = pamd.Problem([gpu_system(s, pamd) for s in w.systems], w.D, w.beta, w.dt,
                         precision=precision)
     paths = start_paths(w, precision)
@@ -74,7 +80,7 @@ def test_zero_radius_is_the_plain_action(pamd, name, precision):
 
 
 @pytest.mark.parametrize("name,precision", [("lj108", "fp32"), ("ragged", "fp32"),
-                                            ("lj108", "fp64")])
+                                            ("lj108", "fp64"), ("mixed", "fp32")])
 def test_overlaps_match_the_oracle(pamd, parity_report, name, precision):
     w, prob, paths, buf = _setup(pamd, name, precision)
     S0, g0 = pamd.action_grad(prob, buf)
