@@ -474,7 +474,8 @@ def main():
     tuned = None
     if any(s.kind == "lj" for s in w.systems) and not args.no_autotune and not args.only_kernel:
         from paper_1907_09529_gb300 import autotune as at
-        shapes = list(at.candidates(tiles=(32, 64, 96, 128, 160, 192, 224, 256), windows=(8, 12, 16, 24)))
+        shapes = list(at.candidates(tiles=(8, 16, 32, 64, 96, 128, 160, 192, 224, 256),
+                                    windows=(8, 12, 16, 24)))
         best, timings = at.autotune(prob, pos, shapes, reps=2, cache=None)
         tuned = {"tile_steps": best[0], "window_steps": best[4],
                  "ms_per_call": round(timings[json.dumps(best)], 4),
