@@ -3,9 +3,11 @@
 For a problem it times ``pamd_action_grad`` (CUDA events, on the current stream)
 over a grid of candidate shapes -- steps per tile, threads per particle, list
 capacity, Verlet skin (double precision), neighbour-list window (single
-precision) -- and keeps the fastest.  Results do not depend on the
-shape (the candidate order inside every sum is fixed), only the speed does, so
-the choice can be cached per problem signature in a small JSON file.
+precision) -- and keeps the fastest.  Results do not depend on the tile, list
+capacity, skin or window (the candidate order inside every sum is fixed); the
+threads per particle change how a particle's sums are split, so results differ
+by rounding only.  The choice can be cached per problem signature in a small
+JSON file.
 """
 from __future__ import annotations
 
