@@ -278,6 +278,34 @@ def measure_fp32_peak(dev, stream, target_ms=60.0):
     return res
 
 
+def measure_fp64_peak(dev, stream, target_ms=40.0):
+    """FP64 FMA throughput of this GPU (the library's fma.rn.f64 probe: 8 independent
+    dependent chains per thread, two 1024-thread CTAs per SM), best of 3 timed
+    launches after a sizing launch, CUDA events on the launching stream."""
+    import ctypes
+    import torch
+    from paper_1907_09529_gb300 import _lib
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 2 * sms, 1024
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = 200
+    e0.record(stream)
+    _lib.pamd_fp64_fma_probe(blocks, threads, iters, ctypes.c_void_p(out.data_ptr()), sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    iters = max(50, int(iters * target_ms / max(e0.elapsed_time(e1), 1e-3)))
+    best = 0.0
+    for _ in range(3):
+        e0.record(stream)
+        fl = _lib.pamd_fp64_fma_probe(blocks, threads, iters, ctypes.c_void_p(out.data_ptr()), sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return {"sms": sms, "blocks": blocks, "threads": threads, "fp64_tflops": best}
+
+
 def host_facts():
     """CPU placement of this process (the host side of the end-to-end copies)."""
     facts = {"cpus": os.cpu_count()}
@@ -678,6 +706,13 @@ def main():
                  "batched_fp32_ms_per_call": ms_kernel,
                  "speedup_batched_vs_plain": ms64 / ms_kernel,
                  "fp32_vs_fp64_rel_err_S": relS, "fp32_vs_fp64_rel_err_grad": relG}
+        if has_lj:  # the plain form against the measured FP64 rate (same algorithmic flops)
+            p64peak = measure_fp64_peak(dev, stream)
+            a64 = flops / (ms64 * 1e-3) / 1e12
+            plain["roofline"] = {"bound": "fp64", "achieved": a64,
+                                 "peak": p64peak["fp64_tflops"], "unit": "TFLOP/s",
+                                 "frac": a64 / p64peak["fp64_tflops"],
+                                 "peak_note": "of measured: FP64 FMA probe in this run"}
         del pos64, S64, g64
 
     cpu = None

@@ -451,6 +451,15 @@ int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void* pos, doubl
 int pamd_fp32_fma_probe(int packed, int blocks, int threads, int iters, float* out,
                         double* flops, void* stream);
 
+/* Measured FP64 fused multiply-add throughput, the rate that bounds the plain
+ * double-precision form (a diagnostic, as above): 8 independent chains of
+ * `iters` dependent fma.rn.f64 per thread.
+ *   out   : double[blocks * threads], device memory, written.
+ *   flops : host double, written (FMA = 2 flops); may be NULL.
+ * PAMD_ERR_ARG as for pamd_fp32_fma_probe. */
+int pamd_fp64_fma_probe(int blocks, int threads, int iters, double* out, double* flops,
+                        void* stream);
+
 /* Bounds checks of the debug build (a diagnostic; the paper has no counterpart).
  * libpamd_debug.so is this library compiled with -DPAMD_DEBUG: every array
  * index of the Lennard-Jones, oscillator, update and multilevel-sampler kernels

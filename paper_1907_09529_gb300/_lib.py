@@ -37,7 +37,7 @@ EXPORTS = (
     "pamd_lj_pair_counts", "pamd_philox", "pamd_normals", "pamd_status_string",
     "pamd_release_cache", "pamd_version", "pamd_tune", "pamd_ho_action_grad_noalloc",
     "pamd_device_status", "pamd_fragment_mc", "pamd_shift_regenerate", "pamd_event",
-    "pamd_cache_stats", "pamd_fp32_fma_probe", "pamd_pipeline_timeline",
+    "pamd_cache_stats", "pamd_fp32_fma_probe", "pamd_fp64_fma_probe", "pamd_pipeline_timeline",
     "pamd_mala_propose", "pamd_mala_reverse", "pamd_mala_accept", "pamd_mala_commit",
     "pamd_debug_status", "pamd_action_grad_hs",
 )
@@ -117,6 +117,8 @@ def load(path: str = LIB_PATH):
             "pamd_pipeline_timeline": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
             "pamd_fp32_fma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, _VP, _VP, _VP]),
+            "pamd_fp64_fma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   _VP, _VP, _VP]),
             "pamd_fragment_mc": (ctypes.c_int, [_PP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 u64, u64, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
             "pamd_shift_regenerate": (ctypes.c_int, [_PP, _VP, _VP, ctypes.c_int, _VP, u64, u64,
@@ -256,6 +258,14 @@ def pamd_fp32_fma_probe(packed, blocks, threads, iters, out, stream):
     """Launch the FMA throughput probe; returns the flops it performs."""
     flops = ctypes.c_double(0.0)
     _call("pamd_fp32_fma_probe", int(packed), int(blocks), int(threads), int(iters), out,
+          ctypes.byref(flops), stream)
+    return flops.value
+
+
+def pamd_fp64_fma_probe(blocks, threads, iters, out, stream):
+    """Launch the FP64 FMA throughput probe; returns the flops it performs."""
+    flops = ctypes.c_double(0.0)
+    _call("pamd_fp64_fma_probe", int(blocks), int(threads), int(iters), out,
           ctypes.byref(flops), stream)
     return flops.value
 
