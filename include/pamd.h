@@ -183,7 +183,8 @@ int pamd_action_grad(const pamd_problem* prob, const void* pos, double* S, void*
  *   sigma_hs : device double array: for every PAMD_LJ system in order, its T+1
  *           radii sigma_HS(0..T) (harmonic systems take none).
  * Harmonic systems get their plain action.  Device pointers only
- * (PAMD_ERR_ARG otherwise).  Combined with the pamd_mala_* pieces, a proposal
+ * (PAMD_ERR_ARG otherwise); whole paths only (PAMD_ERR_UNSUPPORTED for a time
+ * slab).  Combined with the pamd_mala_* pieces, a proposal
  * with an overlapping pair has S' = +inf and is rejected.  The trial paths the
  * paper draws from a hard-sphere propagator are not part of this library. */
 int pamd_action_grad_hs(const pamd_problem* prob, const void* pos, const double* sigma_hs,

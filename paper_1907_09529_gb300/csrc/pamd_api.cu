@@ -1132,6 +1132,7 @@ int pamd_action_grad_hs(const pamd_problem* prob, const void* pos, const double*
     NvtxRange nvtx_("pamd_action_grad_hs");
     int rc = check_em_problem(prob);
     if (rc) return rc;
+    if ((rc = check_whole_paths(prob))) return rc;
     if (!pos || !sigma_hs || !S) return PAMD_ERR_ARG;
     for (const void* b : {pos, (const void*)sigma_hs, (const void*)S, (const void*)grad})
         if (b && is_host_ptr(b)) return PAMD_ERR_ARG;  // device buffers only

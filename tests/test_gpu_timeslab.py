@@ -125,3 +125,8 @@ def test_slab_problems_are_refused_where_whole_paths_are_needed(pamd):
     assert ei.value.status == -2
     with pytest.raises(pamd.PamdError):
         pamd.euler_reference(lp, b)
+    sig = torch.zeros(sum(s.T + 1 for s in lp.systems if s.kind == "lj"), dtype=torch.float64,
+                      device="cuda")
+    with pytest.raises(pamd.PamdError) as ei:
+        pamd.action_grad_hs(lp, b, sig)
+    assert ei.value.status == -2
