@@ -306,13 +306,18 @@ int max_dynamic_smem()
     return v;
 }
 
-// Block size of a class of LJ systems: its largest N rounded up to a warp
-// multiple (at least 128).
+// Block size of a class of LJ systems: its largest N times the threads per
+// particle -- the forced count, else the largest power of two up to 8 that fits
+// 512 threads, so that small systems are spread over more warps -- rounded up to
+// a warp multiple, at least 128 and at most 1024.
 int choose_lj_block(int nmax)
 {
-    int NT = std::max(128, ((nmax + 31) / 32) * 32);
-    if (g_tune_override.tpp > 0) NT = std::max(NT, std::min(1024, ((nmax * g_tune_override.tpp + 31) / 32) * 32));
-    return NT;
+    int tpp = 1;
+    if (g_tune_override.tpp > 0)
+        tpp = g_tune_override.tpp;
+    else
+        while (tpp < 8 && nmax * tpp * 2 <= 512) tpp *= 2;
+    return std::max(128, std::min(1024, ((nmax * tpp + 31) / 32) * 32));
 }
 
 // Per-system LJ launch shape: threads per particle (largest power of two <= 8

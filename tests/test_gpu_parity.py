@@ -184,10 +184,10 @@ def test_threads_per_particle_match_the_oracle(pamd, tpp):
 @pytest.mark.parametrize("one_class", [False, True])
 def test_block_size_classes_match_the_oracle(pamd, parity_report, one_class):
     """A single-precision batch of LJ systems with N on both sides of 512 runs in two
-    persistent launches (the N <= 512 systems in 128-thread blocks with the pipelined
-    gradient pass, the others in 704-thread blocks); PAMD_LJ_ONE_CLASS keeps one
-    launch of 704-thread blocks.  Both against the oracle, and in one chain per
-    launch."""
+    persistent launches (the N <= 512 system in 384-thread blocks, four threads per
+    particle, with the pipelined gradient pass; the others in 704-thread blocks);
+    PAMD_LJ_ONE_CLASS keeps one launch of 704-thread blocks.  Both against the
+    oracle, and in one chain per launch."""
     import os
     w = _workload("mixed")
     paths = start_paths(w, "fp32")
