@@ -567,7 +567,7 @@ def main():
         hS = S.cpu().pin_memory()
         hacc = torch.zeros(prob.n_chains, dtype=torch.int32).pin_memory()
         pamd.path_update(prob, hpos, hgrad, hS, h, 1, seed=seed, counter=5, n_accepted=hacc)
-        ne = max(3, min(args.steps, 10))
+        ne = max(3, args.steps)  # the same number of steps as the device-timed region
         # pinned copy rates of this host link, measured on the same buffers (they vary
         # between machines and bound the end-to-end time)
         scratch = torch.empty_like(pos)
