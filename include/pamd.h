@@ -36,7 +36,9 @@
  * With device pointers every call is asynchronous on `stream`.  Device
  * buffers must be 16-byte aligned, and are read in whole 16-byte units: a
  * buffer must stay readable up to its end rounded up to 16 bytes (any
- * cudaMalloc'd buffer is).
+ * cudaMalloc'd buffer is).  A device path, gradient, noise or trajectory
+ * buffer that is not 16-byte aligned (a view at an odd element offset) is
+ * refused with PAMD_ERR_ARG before any other check and before anything runs.
  *
  * Errors.  Every entry point returns PAMD_OK (0) or a negative status; no
  * C++ exception crosses this boundary.  On error nothing is guaranteed

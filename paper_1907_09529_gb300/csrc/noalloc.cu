@@ -152,6 +152,7 @@ int run_noalloc(const pamd_problem* p, const R* pos, double* S, R* grad, double*
 extern "C" int pamd_ho_action_grad_noalloc(const pamd_problem* prob, const void* pos, double* S,
                                            void* grad, void* stream)
 {
+    if (pamd::any_misaligned({pos, grad})) return PAMD_ERR_ARG;
     if (!prob || !prob->systems || prob->n_systems <= 0 || !pos || !S || !grad) return PAMD_ERR_ARG;
     if (prob->precision != PAMD_FP32 && prob->precision != PAMD_FP64) return PAMD_ERR_ARG;
     if (!(prob->D > 0) || !(prob->dt > 0) || !(prob->beta > 0)) return PAMD_ERR_ARG;

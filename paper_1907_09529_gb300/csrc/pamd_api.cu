@@ -1093,6 +1093,7 @@ static int action_common(const pamd_problem* prob, const void* pos, double* S, v
                          bool with_grad, void* stream)
 {
     NvtxRange nvtx_(with_grad ? "pamd_action_grad" : "pamd_action");
+    if (any_misaligned({pos, grad})) return PAMD_ERR_ARG;
     int rc = check_em_problem(prob);
     if (rc) return rc;
     if (!pos || !S || (with_grad && !grad)) return PAMD_ERR_ARG;
@@ -1135,6 +1136,7 @@ int pamd_action_grad_hs(const pamd_problem* prob, const void* pos, const double*
                         void* grad, void* stream)
 {
     NvtxRange nvtx_("pamd_action_grad_hs");
+    if (any_misaligned({pos, grad})) return PAMD_ERR_ARG;
     int rc = check_em_problem(prob);
     if (rc) return rc;
     if ((rc = check_whole_paths(prob))) return rc;
@@ -1197,6 +1199,7 @@ int pamd_path_update(const pamd_problem* prob, void* pos, void* grad, double* S,
                      const double* log_u, int* n_accepted, double* log_alpha, void* stream)
 {
     NvtxRange nvtx_("pamd_path_update");
+    if (any_misaligned({pos, grad, noise})) return PAMD_ERR_ARG;
     int rc = check_em_problem(prob);
     if (rc) return rc;
     if ((rc = check_whole_paths(prob))) return rc;
@@ -1334,6 +1337,7 @@ int pamd_mala_propose(const pamd_problem* prob, const void* pos, const void* gra
                       void* stream)
 {
     NvtxRange nvtx_("pamd_mala_propose");
+    if (any_misaligned({pos, grad, prop, noise})) return PAMD_ERR_ARG;
     if (!(h > 0) || (noise && is_host_ptr(noise))) return PAMD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mutex);
     Plan* P;
@@ -1358,6 +1362,7 @@ int pamd_mala_reverse(const pamd_problem* prob, const void* pos, const void* pro
                       const void* grad_prop, double h, double* q_rev, void* stream)
 {
     NvtxRange nvtx_("pamd_mala_reverse");
+    if (any_misaligned({pos, prop, grad_prop})) return PAMD_ERR_ARG;
     if (!(h > 0)) return PAMD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mutex);
     Plan* P;
@@ -1402,6 +1407,7 @@ int pamd_mala_commit(const pamd_problem* prob, void* pos, void* grad, double* S,
                      const void* grad_prop, const double* S_prop, const int* accept, void* stream)
 {
     NvtxRange nvtx_("pamd_mala_commit");
+    if (any_misaligned({pos, grad, prop, grad_prop})) return PAMD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mutex);
     Plan* P;
     int rc = mala_piece_plan(prob, {pos, grad, S, prop, grad_prop, S_prop, accept}, &P);
@@ -1423,6 +1429,7 @@ int pamd_euler_reference(const pamd_problem* prob, void* pos, uint64_t seed, uin
                          const void* noise, void* stream)
 {
     NvtxRange nvtx_("pamd_euler_reference");
+    if (any_misaligned({pos, noise})) return PAMD_ERR_ARG;
     int rc = check_em_problem(prob);
     if (rc) return rc;
     if ((rc = check_whole_paths(prob))) return rc;
@@ -1484,6 +1491,7 @@ int pamd_fragment_mc(const pamd_problem* prob, void* pos, int l_min, int l_max, 
                      void* stream)
 {
     NvtxRange nvtx_("pamd_fragment_mc");
+    if (any_misaligned({pos, noise})) return PAMD_ERR_ARG;
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_whole_paths(prob))) return rc;
@@ -1534,6 +1542,7 @@ int pamd_event(const pamd_problem* prob, void* pos, void* pos_out, int n_sample,
                int* n_proposed, void* stream)
 {
     NvtxRange nvtx_("pamd_event");
+    if (any_misaligned({pos, pos_out, traj})) return PAMD_ERR_ARG;
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_whole_paths(prob))) return rc;
@@ -1600,6 +1609,7 @@ int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_o
                           void* stream)
 {
     NvtxRange nvtx_("pamd_shift_regenerate");
+    if (any_misaligned({pos, pos_out, traj, noise})) return PAMD_ERR_ARG;
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_whole_paths(prob))) return rc;
@@ -1632,6 +1642,7 @@ int pamd_shift_regenerate(const pamd_problem* prob, const void* pos, void* pos_o
 int pamd_lj_pair_counts(const pamd_problem* prob, const void* pos, long long* counts, void* stream)
 {
     NvtxRange nvtx_("pamd_lj_pair_counts");
+    if (any_misaligned({pos})) return PAMD_ERR_ARG;
     int rc = check_problem(prob);
     if (rc) return rc;
     if ((rc = check_whole_paths(prob))) return rc;

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdint>
+#include <initializer_list>
+
 #include "pamd.h"
 
 namespace pamd {
@@ -216,6 +219,28 @@ __device__ __forceinline__ double block_sum(double v, double* scratch)
         s = warp_sum(s);
     }
     return s;
+}
+
+// A device buffer whose address is not 16-byte aligned: the element kernels read
+// and write whole 16-byte units, so such a buffer is refused (PAMD_ERR_ARG) before
+// anything is launched.  Host buffers are staged into the library's own aligned
+// workspace and pass.  Asks the driver only about a misaligned address.
+inline bool misaligned_device_buffer(const void* p)
+{
+    if (!p || (reinterpret_cast<uintptr_t>(p) & 15u) == 0) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline bool any_misaligned(std::initializer_list<const void*> ps)
+{
+    for (const void* p : ps)
+        if (misaligned_device_buffer(p)) return true;
+    return false;
 }
 
 // ------------------------------------------------------------------ work descriptors

@@ -9,6 +9,8 @@
 //   q_fwd = sum_{t>=1} |x'_t - x_t + h g_t(x)|^2,  q_rev = sum_{t>=1} |x_t - x'_t + h g_t(x')|^2
 // accepted iff log u < log alpha.  Element-wise terms are formed in the data
 // precision from the stored values; every sum and the comparison are double.
+#include <type_traits>
+
 #include "pamd_internal.cuh"
 
 namespace pamd {
@@ -70,6 +72,9 @@ cudaError_t launch_set_mala_params(MalaDev* md, uint64_t seed, uint64_t counter,
 // element e is component (g & 3) of the Philox call for group g >> 2, g = e_glob + e
 // its whole-path index (one call per group on whole paths).  Elements outside
 // [s, own_hi) -- the fixed tail x_0 or a time slab's halo slices -- are copied.
+// A group of four free elements of a single-precision whole path on a 16-byte
+// aligned block moves as float4 loads and one float4 store, with the arithmetic of
+// the elements in the same order as the element-wise loop (bitwise the same).
 template <typename R, bool SLAB>
 __global__ void __launch_bounds__(kElemThreads)
     mala_propose_kernel(const ElemBlock* __restrict__ blocks, const R* __restrict__ pos,
@@ -84,12 +89,32 @@ __global__ void __launch_bounds__(kElemThreads)
     const long long base = B.chain_base;
     R acc = R(0);
     const int ng = (B.n + 3) >> 2;             // e0 is a multiple of 4
+    const bool vec = std::is_same<R, float>::value && !SLAB && ((base + B.e0) & 3) == 0;
     for (int gq = threadIdx.x; gq < ng; gq += kElemThreads) {
         float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         long long zg = -1;                     // Philox group held in z4 (time slabs)
         if (!SLAB && !noise)                   // whole paths: the group of the 4 elements
             z4 = philox_normals4(seed, counter, kStreamMala, (uint32_t)B.chain,
                                  (uint32_t)((B.e0 >> 2) + gq));
+        if constexpr (std::is_same<R, float>::value) {
+            const int e4 = B.e0 + 4 * gq;
+            if (vec && e4 + 3 < B.e0 + B.n && e4 >= B.s && PAMD_OK_IDX(e4 + 3, B.chain_len)) {
+                const float4 x4 = __ldg(reinterpret_cast<const float4*>(pos + base + e4));
+                const float4 g4 = __ldg(reinterpret_cast<const float4*>(grad + base + e4));
+                if (noise) z4 = __ldg(reinterpret_cast<const float4*>(noise + base + e4));
+                const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, gs[4] = {g4.x, g4.y, g4.z, g4.w},
+                            zs[4] = {z4.x, z4.y, z4.z, z4.w};
+                float ps[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    ps[l] = xs[l] + fma_r(-h, gs[l], s2h * zs[l]);
+                    const float f = fma_r(h, gs[l], ps[l] - xs[l]);
+                    acc = fma_r(f, f, acc);
+                }
+                *reinterpret_cast<float4*>(prop + base + e4) = make_float4(ps[0], ps[1], ps[2], ps[3]);
+                continue;
+            }
+        }
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             const int e = B.e0 + 4 * gq + l;

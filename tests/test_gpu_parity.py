@@ -507,6 +507,47 @@ def test_invalid_arguments_are_rejected(pamd):
         pamd.path_update(prob, buf, buf.clone(), S, h=-1.0)
 
 
+def test_misaligned_device_buffers_are_refused(pamd):
+    """A device buffer at an address that is not 16-byte aligned is refused with
+    PAMD_ERR_ARG by every entry point that takes path-shaped buffers, before any
+    other check: each problem here is also unsupported (an LJ system of N = 2000,
+    an oscillator slice of 9000 elements for the allocation-free call), so a
+    missing alignment check would report PAMD_ERR_UNSUPPORTED instead, still
+    without launching anything."""
+    import ctypes
+    from paper_1907_09529_gb300 import _lib
+    lj = pamd.Problem([pamd.System("lj", 2000, 3, 2, 1, box=20.0, rc=2.5)], 1.0, 1.0, 1e-4)
+    base = torch.zeros(lj.span + 64, dtype=torch.float32, device="cuda")
+    bad = base[1:]  # 4 bytes past a 16-byte boundary
+    assert bad.data_ptr() % 16 == 4
+    good = torch.zeros_like(base)
+    S = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sig = torch.zeros(3, dtype=torch.float64, device="cuda")
+    calls = [lambda: pamd.action(lj, bad),
+             lambda: pamd.action_grad(lj, bad),
+             lambda: pamd.action_grad(lj, good, S, bad),
+             lambda: pamd.action_grad_hs(lj, bad, sig),
+             lambda: pamd.path_update(lj, bad, good, S, 1e-6),
+             lambda: pamd.euler_reference(lj, bad),
+             lambda: pamd.mala_propose(lj, good, good, 1e-6, prop=bad),
+             lambda: pamd.mala_reverse(lj, good, bad, good, 1e-6),
+             lambda: pamd.mala_commit(lj, bad, good, S, good, good, S,
+                                      torch.zeros(1, dtype=torch.int32, device="cuda")),
+             lambda: pamd.lj_pair_counts(lj, bad)]
+    for k, call in enumerate(calls):
+        with pytest.raises(pamd.PamdError) as ei:
+            call()
+        assert ei.value.status == -1, (k, ei.value.status)
+    ho = pamd.Problem([pamd.System("harmonic", 3000, 3, 2, 1)], 1.0, 1.0, 1e-3)
+    hbase = torch.zeros(ho.span + 64, dtype=torch.float32, device="cuda")
+    with pytest.raises(pamd.PamdError) as ei:
+        _lib.pamd_ho_action_grad_noalloc(ho.ref, ctypes.c_void_p(hbase[1:].data_ptr()),
+                                         ctypes.c_void_p(S.data_ptr()),
+                                         ctypes.c_void_p(hbase.data_ptr()), None)
+    assert ei.value.status == -1
+    torch.cuda.synchronize()
+
+
 def test_nonfinite_action_is_reported(pamd):
     """Two particles on top of each other give an infinite action; the library
     flags it on the device and pamd_device_status reports it once."""
