@@ -430,10 +430,16 @@ def run_sampler(args, w, pamd, prob, dev, rank, world):
 
 
 def launches_per_update(prob):
-    n_lj = sum(1 for s in prob.systems if s.kind == "lj")
-    n_ho = 1 if any(s.kind == "harmonic" for s in prob.systems) else 0
-    # propose, [harmonic action], LJ action per system, finalize S, reverse,
-    # finalize q_fwd, finalize q_rev, accept, commit
+    """Kernels of one path update: propose, one action launch per harmonic system,
+    one LJ launch per block-size class (two when a single-precision batch mixes
+    N <= 512 and N > 512), finalize S, reverse, finalize q_fwd and q_rev, accept,
+    commit."""
+    n_ho = sum(1 for s in prob.systems if s.kind == "harmonic")
+    lj = [s.N for s in prob.systems if s.kind == "lj"]
+    n_lj = 0
+    if lj:
+        mixed = min(lj) <= 512 < max(lj) and prob.precision == "fp32"
+        n_lj = 2 if mixed else 1
     return 1 + n_ho + n_lj + 1 + 1 + 2 + 1 + 1
 
 
