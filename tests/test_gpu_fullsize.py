@@ -67,17 +67,25 @@ def test_ho3d_full_size(pamd, parity_report):
                                  grad_rel_maxabs=em)
 
 
-def test_lj500_full_size(pamd, parity_report):
-    """LJ N = 500, T = 16384, 8 chains (oracle Euler-Maruyama start paths): every
-    chain's S, and the gradient at 48 sampled slices per chain, incl. both ends."""
+@pytest.fixture(scope="module")
+def lj500_paths():
+    """LJ N = 500, T = 16384, 8 chains: the oracle's Euler-Maruyama start paths
+    (rounded to float32), shared by the full-size lj500 tests."""
     w = inputs.workload("lj500")
     spec = w.systems[0]
     pot = oracle_potential(spec)
-    nth = oracle.max_threads()
     x0 = inputs.initial_positions(spec, 1)
     xi = inputs.euler_noise(spec, w.seed)
-    paths = oracle.euler_batch(pot, x0, xi, w.D, w.beta, w.dt, store_f32=True, nthreads=nth)
-    del xi
+    paths = oracle.euler_batch(pot, x0, xi, w.D, w.beta, w.dt, store_f32=True,
+                               nthreads=oracle.max_threads())
+    return w, spec, pot, paths
+
+
+def test_lj500_full_size(pamd, parity_report, lj500_paths):
+    """LJ N = 500, T = 16384, 8 chains (oracle Euler-Maruyama start paths): every
+    chain's S, and the gradient at 48 sampled slices per chain, incl. both ends."""
+    w, spec, pot, paths = lj500_paths
+    nth = oracle.max_threads()
     prob = _problem(pamd, w)
     buf = prob.empty("cuda")
     prob.view(buf, 0).copy_(torch.from_numpy(paths).float())
@@ -99,6 +107,43 @@ def test_lj500_full_size(pamd, parity_report):
         parity_report.record("lj500", "test_lj500_full_size (S of every chain; gradient at "
                              "48 sampled slices per chain)", S_rel=es, grad_rel_2norm=eg,
                              grad_rel_maxabs=em)
+
+
+def test_lj500_hardsphere_full_size(pamd, parity_report, lj500_paths):
+    """The hard-sphere path bias at full size: radii at 98 sampled slices (the tail
+    and the nose among them) at four levels around the liquid's closest approach.
+    Every chain's overlap decision equals the oracle's mirror of the kernels'
+    single-precision rule at those slices, a finite S is the plain action bit for
+    bit, and both outcomes occur."""
+    w, spec, pot, paths = lj500_paths
+    prob = _problem(pamd, w)
+    buf = prob.empty("cuda")
+    prob.view(buf, 0).copy_(torch.from_numpy(paths).float())
+    S0, _ = pamd.action_grad(prob, buf)
+    torch.cuda.synchronize()
+    S0 = S0.cpu().numpy()
+    rng = inputs.rng(321)
+    ts = np.unique(np.concatenate([[0, spec.T], rng.integers(1, spec.T, 96)]))
+    n_inf = n_fin = 0
+    for level in (0.75, 0.85, 0.90, 0.95):
+        sig = np.zeros(spec.T + 1)
+        sig[ts] = level
+        S, _ = pamd.action_grad_hs(prob, buf, torch.from_numpy(sig).cuda(), with_grad=False)
+        torch.cuda.synchronize()
+        S = S.cpu().numpy()
+        for b in range(spec.n_chains):
+            x32 = paths[b].astype(np.float32)
+            want = any(oracle.hs_overlap_f32(spec.box, spec.rc_eff, level, x32[t]) for t in ts)
+            if want:
+                assert S[b] == math.inf, (level, b)
+                n_inf += 1
+            else:
+                assert S[b] == S0[b], (level, b)
+                n_fin += 1
+    assert n_inf > 0 and n_fin > 0
+    parity_report.record("lj500_hardsphere", "test_lj500_hardsphere_full_size (overlap "
+                         "decisions equal at 98 sampled slices, four radii)",
+                         chains_infinite=n_inf, chains_finite=n_fin)
 
 
 def test_lj108_full_size(pamd, parity_report):
