@@ -146,6 +146,32 @@ def test_lj500_hardsphere_full_size(pamd, parity_report, lj500_paths):
                          chains_infinite=n_inf, chains_finite=n_fin)
 
 
+def test_lj500_timeslabs_full_size(pamd, parity_report, lj500_paths):
+    """One lj500 path split into four time slabs held by this process, at full size:
+    the gradient at every owned slice equals the whole-path call's bit for bit, and
+    each chain's S (the slabs' FP64 parts summed) agrees to 1e-12."""
+    from paper_1907_09529_gb300 import timeslab
+    w, spec, pot, paths = lj500_paths
+    prob = _problem(pamd, w)
+    buf = prob.empty("cuda")
+    prob.view(buf, 0).copy_(torch.from_numpy(paths).float())
+    S_ref, g_ref = pamd.action_grad(prob, buf)
+    run = timeslab.SlabRun(prob, timeslab.LocalComm(4))
+    bufs = [timeslab.scatter(prob, buf, lp) for lp in run.probs]
+    S, G = run.action_grad(bufs)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for k, lp in enumerate(run.probs):
+        worst = max(worst, float(((S[k] - S_ref).abs() / S_ref.abs()).max()))
+        s = lp.systems[0]
+        o = timeslab.owned_slices(s)
+        lo, hi = s.first_slice + o.start, s.first_slice + o.stop
+        assert torch.equal(lp.view(G[k], 0)[:, o], prob.view(g_ref, 0)[:, lo:hi]), k
+    assert worst <= 1e-12
+    parity_report.record("lj500_timeslab4", "test_lj500_timeslabs_full_size (S vs the whole-path "
+                         "call; owned gradients bitwise)", S_rel=worst)
+
+
 def test_lj108_full_size(pamd, parity_report):
     """LJ N = 108, T = 4096: complete S and gradient."""
     w = inputs.workload("lj108")
